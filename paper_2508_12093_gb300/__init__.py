@@ -1,0 +1,309 @@
+"""GB300-native RNS-CKKS evaluator for PP-STAT's encrypted statistics.
+
+A thin Python face of the C ABI in include/ppst.h (argument marshalling only:
+every step runs in the CUDA library). PyTorch supplies device memory (through
+its caching allocator) and the CUDA stream; numpy arrays carry host buffers.
+
+    ctx = Context(workloads.PARAMS["n16_d6"])
+    sk, evk = ctx.keygen(seed=2)
+    col = ctx.encrypt_column(evk, x, seed=3)
+    res = ctx.query(evk, PPST_KURT, col, opts=dict(B_x=20, cheb_log2deg=7, newton_steps=3))
+    values, report = ctx.decrypt(sk, res)
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (ERRORS, PPST_CV, PPST_KURT, PPST_PCC, PPST_SKEW, PPST_ZSCORE, lib, ppst_allocator,  # noqa: F401
+                   ppst_params, ppst_qopts, ppst_report)
+
+STATS = {"zscore": PPST_ZSCORE, "cv": PPST_CV, "skew": PPST_SKEW, "kurt": PPST_KURT, "pcc": PPST_PCC}
+
+
+class PpstError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _u64(a):
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    return a, a.ctypes.data_as(_lib.u64p)
+
+
+class _Handle:
+    def __init__(self, ctx, ptr):
+        self.ctx, self.ptr = ctx, ptr
+
+    def close(self):
+        if self.ptr:
+            lib.ppst_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SecretKey(_Handle):
+    pass
+
+
+class EvalKeys(_Handle):
+    pass
+
+
+class Ciphertext(_Handle):
+    @property
+    def level(self):
+        lv, sc = _lib.c_u32(), ctypes.c_double()
+        lib.ppst_ct_level(self.ptr, ctypes.byref(lv), ctypes.byref(sc))
+        return lv.value
+
+    @property
+    def scale(self):
+        lv, sc = _lib.c_u32(), ctypes.c_double()
+        lib.ppst_ct_level(self.ptr, ctypes.byref(lv), ctypes.byref(sc))
+        return sc.value
+
+
+class Column(_Handle):
+    def __init__(self, ctx, ptr, n):
+        super().__init__(ctx, ptr)
+        self.n = n
+
+
+class Result(_Handle):
+    def cts(self):
+        n = _lib.c_u32()
+        lib.ppst_res_count(self.ptr, ctypes.byref(n))
+        out = []
+        for i in range(n.value):
+            p = ctypes.c_void_p()
+            lib.ppst_res_ct(self.ptr, i, ctypes.byref(p))
+            out.append(_View(self.ctx, p.value, self))
+        return out
+
+
+class _View(Ciphertext):
+    """A ciphertext owned by a Result (not freed on its own)."""
+
+    def __init__(self, ctx, ptr, owner):
+        self.ctx, self.ptr, self._owner = ctx, ptr, owner
+
+    def close(self):
+        self.ptr = None
+
+
+def _opts(o):
+    if o is None:
+        o = {}
+    if isinstance(o, ppst_qopts):
+        return o
+    return ppst_qopts(float(o.get("B_x", 1.0)), float(o.get("B_y", 1.0)), int(o.get("cheb_log2deg", 7)),
+                      int(o.get("newton_steps", 3)))
+
+
+class Context:
+    """One parameter set on one GPU stream (not thread-safe)."""
+
+    def __init__(self, params, use_torch=True, stream=None):
+        self.params = dict(params)
+        prm = ppst_params(params["log_n"], params["n_q"], params["n_p"], params["dnum"], params["q0_bits"],
+                          params["q_bits"], params["p_bits"], float(params["log_scale"]),
+                          float(params.get("sigma", 0.0)), int(params.get("gauss_bound", 0)))
+        self._alloc = None
+        if use_torch:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("CUDA is not available: the library has no CPU path")
+            dev = torch.cuda.current_device()
+            self.stream = torch.cuda.current_stream().cuda_stream if stream is None else int(stream)
+
+            def _alloc(user, nbytes, strm):
+                return torch.cuda.caching_allocator_alloc(nbytes, dev, strm or 0)
+
+            def _release(user, ptr, nbytes, strm):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._cb = (_lib.ALLOC_FN(_alloc), _lib.RELEASE_FN(_release))
+            self._alloc = ppst_allocator(self._cb[0], self._cb[1], None)
+        else:
+            self.stream = 0 if stream is None else int(stream)
+        out = ctypes.c_void_p()
+        rc = lib.ppst_ctx_create(ctypes.byref(prm), ctypes.byref(self._alloc) if self._alloc else None,
+                                 ctypes.c_void_p(self.stream), ctypes.byref(out))
+        if rc != 0:
+            raise PpstError(rc, "ppst_ctx_create failed")
+        self.ptr = out.value
+        n = _lib.c_u32()
+        lib.ppst_ctx_primes(self.ptr, None, 0, ctypes.byref(n))
+        buf = np.zeros(n.value, dtype=np.uint64)
+        lib.ppst_ctx_primes(self.ptr, buf.ctypes.data_as(_lib.u64p), n.value, ctypes.byref(n))
+        self.primes = [int(v) for v in buf]
+        self.N = 1 << params["log_n"]
+        self.S = self.N // 2
+        self.L = params["n_q"] - 1
+        self.K = params["n_p"]
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib.ppst_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise PpstError(rc, lib.ppst_last_error(self.ptr).decode())
+
+    def _new(self, fn, *args, cls=Ciphertext):
+        out = ctypes.c_void_p()
+        self._check(fn(self.ptr, *args, ctypes.byref(out)))
+        return cls(self, out.value)
+
+    # -- keys / encryption ----------------------------------------------------
+    def keygen(self, seed, rotations=None):
+        sk, evk = ctypes.c_void_p(), ctypes.c_void_p()
+        if rotations:
+            arr = (ctypes.c_int32 * len(rotations))(*rotations)
+            rc = lib.ppst_keygen(self.ptr, seed, arr, len(rotations), ctypes.byref(sk), ctypes.byref(evk))
+        else:
+            rc = lib.ppst_keygen(self.ptr, seed, None, 0, ctypes.byref(sk), ctypes.byref(evk))
+        self._check(rc)
+        return SecretKey(self, sk.value), EvalKeys(self, evk.value)
+
+    def sk_export(self, sk):
+        s = np.zeros(self.N, dtype=np.int64)
+        self._check(lib.ppst_sk_export(self.ptr, sk.ptr, s.ctypes.data_as(_lib.i64p), self.N))
+        return s
+
+    def evk_export(self, evk, which, digit):
+        rows = self.L + 1 + self.K
+        b = np.zeros((rows, self.N), dtype=np.uint64)
+        a = np.zeros((rows, self.N), dtype=np.uint64)
+        self._check(lib.ppst_evk_export(self.ptr, evk.ptr, which, digit, b.ctypes.data_as(_lib.u64p),
+                                        a.ctypes.data_as(_lib.u64p)))
+        return b, a
+
+    def encrypt_column(self, evk, x, seed):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        out = ctypes.c_void_p()
+        self._check(lib.ppst_encrypt_column(self.ptr, evk.ptr, x.ctypes.data_as(_lib.f64p), len(x), seed,
+                                            ctypes.byref(out)))
+        return Column(self, out.value, len(x))
+
+    def encrypt_ints(self, evk, m, seed, index, scale):
+        m = np.ascontiguousarray(m, dtype=np.int64)
+        return self._new(lib.ppst_encrypt_ints, evk.ptr, m.ctypes.data_as(_lib.i64p), seed, index, float(scale))
+
+    def decrypt(self, sk, res, cap=None):
+        if cap is None:
+            cap = max(1, getattr(res, "n", 1))
+        out = np.zeros(cap, dtype=np.float64)
+        n = ctypes.c_size_t()
+        rep = ppst_report()
+        self._check(lib.ppst_decrypt(self.ptr, sk.ptr, res.ptr, out.ctypes.data_as(_lib.f64p), cap,
+                                     ctypes.byref(n), ctypes.byref(rep)))
+        report = dict(level_in=rep.level_in, level_out=rep.level_out, depth_used=rep.depth_used,
+                      scale=rep.scale, n_cts=rep.n_cts)
+        return out[:min(cap, n.value)], report
+
+    def decrypt_ct(self, sk, ct):
+        out = np.zeros(self.S, dtype=np.float64)
+        self._check(lib.ppst_decrypt_ct(self.ptr, sk.ptr, ct.ptr, out.ctypes.data_as(_lib.f64p), self.S))
+        return out
+
+    # -- statistics -----------------------------------------------------------
+    def query(self, evk, stat, x, y=None, opts=None):
+        stat = STATS.get(stat, stat)
+        o = _opts(opts)
+        out = ctypes.c_void_p()
+        self._check(lib.ppst_query(self.ptr, evk.ptr, stat, x.ptr, y.ptr if y is not None else None,
+                                   ctypes.byref(o), ctypes.byref(out)))
+        r = Result(self, out.value)
+        r.n = x.n if stat == PPST_ZSCORE else 1
+        return r
+
+    def query_batch(self, evk, queries):
+        """queries: list of (stat, x, y_or_None, opts)."""
+        n = len(queries)
+        stats = (ctypes.c_int * n)(*[STATS.get(q[0], q[0]) for q in queries])
+        xs = (ctypes.c_void_p * n)(*[q[1].ptr for q in queries])
+        ys = (ctypes.c_void_p * n)(*[(q[2].ptr if q[2] is not None else None) for q in queries])
+        opts = (ppst_qopts * n)(*[_opts(q[3]) for q in queries])
+        outs = (ctypes.c_void_p * n)()
+        self._check(lib.ppst_query_batch(self.ptr, evk.ptr, n, stats, xs, ys, opts, outs))
+        res = []
+        for q, p in zip(queries, outs):
+            r = Result(self, p)
+            r.n = q[1].n if STATS.get(q[0], q[0]) == PPST_ZSCORE else 1
+            res.append(r)
+        return res
+
+    def col_from_cts(self, cts, n_rows):
+        arr = (ctypes.c_void_p * len(cts))(*[c.ptr for c in cts])
+        out = ctypes.c_void_p()
+        self._check(lib.ppst_col_from_cts(self.ptr, arr, len(cts), n_rows, ctypes.byref(out)))
+        return Column(self, out.value, n_rows)
+
+    # -- ciphertext ops -------------------------------------------------------------
+    def ct_import(self, c0, c1, level, scale):
+        c0, p0 = _u64(c0)
+        c1, p1 = _u64(c1)
+        assert c0.shape == (level + 1, self.N) and c1.shape == c0.shape
+        return self._new(lib.ppst_ct_import, p0, p1, level, float(scale))
+
+    def ct_export(self, ct):
+        lv, sc = _lib.c_u32(), ctypes.c_double()
+        self._check(lib.ppst_ct_export(self.ptr, ct.ptr, None, None, ctypes.byref(lv), ctypes.byref(sc)))
+        c0 = np.zeros((lv.value + 1, self.N), dtype=np.uint64)
+        c1 = np.zeros_like(c0)
+        self._check(lib.ppst_ct_export(self.ptr, ct.ptr, c0.ctypes.data_as(_lib.u64p), c1.ctypes.data_as(_lib.u64p),
+                                       ctypes.byref(lv), ctypes.byref(sc)))
+        return c0, c1, lv.value, sc.value
+
+    def hmult(self, evk, a, b):
+        return self._new(lib.ppst_hmult, evk.ptr, a.ptr, b.ptr)
+
+    def rotate(self, evk, a, r):
+        return self._new(lib.ppst_rotate, evk.ptr, a.ptr, r)
+
+    def rotsum(self, evk, a):
+        return self._new(lib.ppst_rotsum, evk.ptr, a.ptr)
+
+    def rescale(self, a):
+        return self._new(lib.ppst_rescale, a.ptr)
+
+    def add(self, a, b):
+        return self._new(lib.ppst_add, a.ptr, b.ptr)
+
+    def sub(self, a, b):
+        return self._new(lib.ppst_sub, a.ptr, b.ptr)
+
+    def add_const(self, a, x):
+        return self._new(lib.ppst_add_const, a.ptr, float(x))
+
+    def mul_const(self, a, x, target=0.0):
+        return self._new(lib.ppst_mul_const, a.ptr, float(x), float(target or 0.0))
+
+    def mul_int(self, a, k):
+        return self._new(lib.ppst_mul_int, a.ptr, int(k))
+
+    def drop(self, a, level):
+        return self._new(lib.ppst_drop, a.ptr, level)
+
+    def sync(self):
+        self._check(lib.ppst_sync(self.ptr))
+
+    def mem_info(self):
+        a, b = ctypes.c_size_t(), ctypes.c_size_t()
+        lib.ppst_mem_info(self.ptr, ctypes.byref(a), ctypes.byref(b))
+        return a.value, b.value

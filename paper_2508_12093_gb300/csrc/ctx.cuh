@@ -1,0 +1,226 @@
+// ctx.cuh -- context, handles and internal entry points of the library.
+#pragma once
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/ppst.h"
+#include "common.cuh"
+
+namespace ppst {
+
+// handle tags (first word of every handle, checked by the C ABI)
+enum Tag : uint32_t {
+    TAG_CTX = 0x50435458u, TAG_SK = 0x50534b30u, TAG_EVK = 0x5045564bu, TAG_CT = 0x50435430u,
+    TAG_COL = 0x50434f4cu, TAG_RES = 0x50524553u, TAG_SRV = 0x50535256u, TAG_DEAD = 0xdeadbeefu
+};
+
+struct Error {
+    int code;
+    std::string msg;
+};
+
+// size-bucketed device memory pool on top of the user's allocator
+struct Pool {
+    ppst_allocator user{};
+    bool has_user = false;
+    cudaStream_t stream = nullptr;
+    std::unordered_map<size_t, std::vector<void *>> free_;
+    size_t in_use = 0, cached = 0;
+    void *get(size_t bytes);
+    void put(void *p, size_t bytes);
+    void trim();
+};
+
+struct Ctx;
+
+struct CtObj {
+    uint32_t tag = TAG_CT;
+    Ctx *ctx = nullptr;
+    uint64_t *d = nullptr;  // [2][L+1][N], evaluation (NTT) domain, limbs 0..level valid
+    int level = 0;
+    double scale = 1.0;
+    uint64_t *c0() const;
+    uint64_t *c1() const;
+};
+
+struct Swk {
+    uint64_t *d = nullptr;  // [dnum][2][L+1+K][N], evaluation domain, Montgomery form (x 2^64)
+};
+
+struct SkObj {
+    uint32_t tag = TAG_SK;
+    Ctx *ctx = nullptr;
+    std::vector<int64_t> s;
+};
+
+struct EvkObj {
+    uint32_t tag = TAG_EVK;
+    Ctx *ctx = nullptr;
+    uint64_t *pk = nullptr;  // [2][L+1][N] evaluation domain, standard form
+    Swk relin;
+    std::map<int, Swk> rot;  // rotation amount (mod N/2) -> Galois key
+    uint64_t seed = 0;
+};
+
+struct ColObj {
+    uint32_t tag = TAG_COL;
+    Ctx *ctx = nullptr;
+    std::vector<CtObj *> cts;
+    size_t n = 0;
+};
+
+struct ResObj {
+    uint32_t tag = TAG_RES;
+    Ctx *ctx = nullptr;
+    std::vector<CtObj *> cts;
+    int stat = 0;
+    size_t n = 0;
+    int level_in = 0;
+};
+
+// host-side per-prime data
+struct HostPrime {
+    uint64_t q, psi;
+};
+
+struct Ctx {
+    uint32_t tag = TAG_CTX;
+    ppst_params prm{};
+    int logN = 0, N = 0, S = 0, L = 0, K = 0, dnum = 0, alpha = 0, np = 0;
+    double scale = 1.0, sigma = 3.2;
+    int gbound = 19;
+    std::vector<uint64_t> primes;  // q_0..q_L, p_0..p_{K-1}
+    std::vector<PrimeC> hpc;       // host copy of the per-prime constants
+    std::vector<uint64_t> psi;
+    PrimeC *d_pc = nullptr;
+    uint64_t *d_tw = nullptr, *d_tw_sh = nullptr, *d_itw = nullptr, *d_itw_sh = nullptr;
+    uint64_t *d_cdt = nullptr;  // discrete Gaussian CDT
+    std::vector<uint64_t> cdt;
+    // key-switching tables (device), offsets per (level, digit)
+    uint64_t *d_ks = nullptr;
+    std::vector<std::vector<size_t>> modup_off;  // [level][digit] -> offset of hatinv (a) | hatinv_sh (a) | hatM (a x ext)
+    size_t moddown_off = 0;                      // hatinvP (K) | hatinvP_sh (K) | hatMP (K x (L+1))
+    ConstVec pinv;                               // P^-1 mod q_i, Shoup
+    std::vector<ConstVec> resc;                  // [level]: q_l^-1 mod q_i, Shoup (i < l)
+    std::vector<ConstVec> resc_qmodv;            // [level]: q_l mod q_i (i < l)
+    std::vector<ConstVec> pmod;                  // [0]: P mod q_t for all primes (gadget), Shoup
+    cudaStream_t stream = nullptr;
+    Pool pool;
+    Error err{0, ""};
+    // workspace (allocated on first key switch)
+    uint64_t *ws_d2 = nullptr;   // [L+1][N]
+    uint64_t *ws_ext = nullptr;  // [dnum][L+1+K][N]
+    uint64_t *ws_acc = nullptr;  // [2][L+1+K][N]
+    uint64_t *ws_conv = nullptr; // [2][L+1][N]
+    size_t ws_bytes = 0;
+
+    size_t ct_words() const { return (size_t)2 * (L + 1) * N; }
+    size_t ext_rows() const { return (size_t)(L + 1 + K); }
+    int ndigits(int level) const { return (level + 1 + alpha - 1) / alpha; }
+    int fail(int code, const std::string &m)
+    {
+        err.code = code;
+        err.msg = m;
+        return code;
+    }
+};
+
+inline uint64_t *CtObj::c0() const { return d; }
+inline uint64_t *CtObj::c1() const { return d + (size_t)(ctx->L + 1) * ctx->N; }
+
+// C++ exception used inside the library, converted to an error code at the ABI
+struct PpstError {
+    int code;
+    std::string msg;
+};
+[[noreturn]] void throw_err(int code, const std::string &m);
+void cuda_check(cudaError_t e, const char *what);
+#define PPST_CUDA(x) ::ppst::cuda_check((x), #x)
+void check_launch(const char *what);
+
+// ---- host math (host_math.cu) ----
+uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t q);
+uint64_t h_powmod(uint64_t b, uint64_t e, uint64_t q);
+uint64_t h_invmod(uint64_t a, uint64_t q);
+uint64_t h_shoup(uint64_t w, uint64_t q);  // floor(w 2^64 / q)
+bool h_is_prime(uint64_t n);
+// exact round-half-away of a double to a signed 128-bit integer (|x| < 2^126)
+__int128 h_round_away(double x);
+// exact round-half-away of (k * m), k double, m integer < 2^62
+__int128 h_round_mul(double k, uint64_t m);
+uint64_t h_mod_i128(__int128 v, uint64_t q);
+
+// ---- context (context.cu) ----
+Ctx *ctx_create(const ppst_params &p, const ppst_allocator *alloc, cudaStream_t stream);
+void ctx_destroy(Ctx *c);
+void ensure_workspace(Ctx &c);
+CtObj *ct_new(Ctx &c, int level, double scale);
+void ct_free(CtObj *ct);
+CtObj *ct_clone(const CtObj &a);
+
+// ---- NTT (ntt.cu) ----
+void ntt_fwd(Ctx &c, const LimbMap &m);
+void ntt_inv(Ctx &c, const LimbMap &m);
+LimbMap map_ct(const Ctx &c, uint64_t *d, int level);  // both polys of a ciphertext buffer
+LimbMap map_poly(const Ctx &c, uint64_t *d, int level); // one poly, limbs 0..level
+
+// ---- kernels (kernels.cu) ----
+void k_add(Ctx &c, const CtObj &a, const CtObj &b, CtObj &out, bool sub);
+void k_neg(Ctx &c, const CtObj &a, CtObj &out);
+void k_mul_scalar_ct(Ctx &c, const CtObj &a, const ConstVec &cv, CtObj &out);
+void k_add_scalar_c0(Ctx &c, const CtObj &a, const ConstVec &cv, CtObj &out);
+void k_tensor(Ctx &c, const CtObj &a, const CtObj &b, int level, uint64_t *d0, uint64_t *d1, uint64_t *d2);
+void k_modup(Ctx &c, const uint64_t *d2coef, int level, uint64_t *ext);
+void k_inner_product(Ctx &c, const uint64_t *ext, const Swk &key, int level, uint64_t *acc);
+void k_moddown(Ctx &c, uint64_t *acc, int level, const uint64_t *add0, const uint64_t *add1, uint64_t *out0,
+               uint64_t *out1);
+void k_rescale(Ctx &c, const CtObj &a, CtObj &out);
+void k_automorph(Ctx &c, const uint64_t *in, int level, uint64_t galois, uint64_t *out, size_t poly_stride,
+                 int npoly);
+void k_copy(Ctx &c, uint64_t *dst, const uint64_t *src, size_t words);
+void k_sample_uniform(Ctx &c, uint64_t seed, uint32_t purpose, uint32_t index, const LimbMap &m);
+void k_sample_small(Ctx &c, uint64_t seed, uint32_t purpose, uint32_t index, bool gauss, int64_t *out);
+void k_small_to_rns(Ctx &c, const int64_t *v, const LimbMap &m);
+void k_swk_combine(Ctx &c, uint64_t *b, const uint64_t *a, const uint64_t *e, const uint64_t *s,
+                   const uint64_t *snew, int digit_lo, int digit_hi);
+void k_pk_combine(Ctx &c, uint64_t *b, const uint64_t *a, const uint64_t *e, const uint64_t *s);
+void k_enc_combine(Ctx &c, const uint64_t *pk, const uint64_t *u, const uint64_t *e0, const uint64_t *e1,
+                   const uint64_t *m, CtObj &out);
+void k_dec_combine(Ctx &c, const CtObj &ct, const uint64_t *s, uint64_t *m);
+void k_to_mont(Ctx &c, uint64_t *d, const LimbMap &m, bool to);
+void k_pointwise_sq(Ctx &c, const uint64_t *a, uint64_t *out, const LimbMap &m);
+
+// ---- evaluator (eval.cu) ----
+CtObj *ev_add(Ctx &c, const CtObj &a, const CtObj &b, bool sub);
+CtObj *ev_add_const(Ctx &c, const CtObj &a, double x);
+CtObj *ev_mul_int(Ctx &c, const CtObj &a, int64_t k);
+CtObj *ev_mul_const(Ctx &c, const CtObj &a, double x, double target);  // target <= 0: keep scale
+CtObj *ev_rescale(Ctx &c, const CtObj &a);
+CtObj *ev_hmult(Ctx &c, const EvkObj &k, const CtObj &a, const CtObj &b);
+CtObj *ev_rotate(Ctx &c, const EvkObj &k, const CtObj &a, int r);
+CtObj *ev_rotsum(Ctx &c, const EvkObj &k, const CtObj &a);
+CtObj *ev_drop(Ctx &c, const CtObj &a, int level);
+uint64_t galois_elt(const Ctx &c, int r);
+
+// ---- keys, encryption, encoding (keys.cu) ----
+void keygen(Ctx &c, uint64_t seed, const std::vector<int> &rots, SkObj *&sk, EvkObj *&evk);
+CtObj *encrypt_ints(Ctx &c, const EvkObj &k, const int64_t *m, uint64_t seed, uint32_t index, double scale);
+void encode(const Ctx &c, const double *z, size_t n, double scale, std::vector<int64_t> &m);
+void decrypt_to_slots(Ctx &c, const SkObj &sk, const CtObj &ct, std::vector<double> &slots);
+void export_ct(Ctx &c, const CtObj &ct, uint64_t *c0, uint64_t *c1);
+CtObj *import_ct(Ctx &c, const uint64_t *c0, const uint64_t *c1, int level, double scale);
+void export_swk(Ctx &c, const Swk &k, int digit, uint64_t *b, uint64_t *a);
+
+// ---- statistics (stats.cu) ----
+struct QueryIn {
+    int stat;
+    const ColObj *x, *y;
+    ppst_qopts o;
+};
+void run_queries(Ctx &c, const EvkObj &k, const std::vector<QueryIn> &qs, std::vector<ResObj *> &out);
+
+}  // namespace ppst

@@ -1,0 +1,180 @@
+// eval.cu -- evaluator operations on device-resident ciphertexts.
+//
+// Ciphertexts stay in the evaluation (NTT) domain. Readings of the CKKS ops
+// the paper uses as a black box (Sec. 3.1):
+//  * HMult = tensor -> hybrid key switch of d2 with the relinearisation key
+//    -> add -> rescale; scale (s_a s_b) / q_l;
+//  * key switch = iNTT(d) -> ModUp (fast base conversion per digit) -> NTT ->
+//    inner product with the key over Q_l u P -> ModDown;
+//  * Rot(r) = automorphism X -> X^(5^r) of (c0, c1) then key switch of the
+//    rotated c1 with the Galois key;
+//  * Mul(P) by a real constant = integer round(k q_l) then rescale (scale kept
+//    or steered to a target); Add(P) = round(c * scale) added to every slot.
+#include <cmath>
+
+#include "ctx.cuh"
+
+namespace ppst {
+
+static void check_scales(double sa, double sb)
+{
+    if (!(std::fabs(sa / sb - 1.0) < 0x1p-20))
+        throw_err(PPST_E_SCALE, "scale mismatch " + std::to_string(sa) + " vs " + std::to_string(sb));
+}
+
+CtObj *ev_add(Ctx &c, const CtObj &a, const CtObj &b, bool sub)
+{
+    const int lv = std::min(a.level, b.level);
+    check_scales(a.scale, b.scale);
+    CtObj *o = ct_new(c, lv, a.scale);
+    k_add(c, a, b, *o, sub);
+    return o;
+}
+
+static ConstVec residues(const Ctx &c, __int128 m, int nl)
+{
+    ConstVec cv;
+    for (int i = 0; i < nl; i++) {
+        cv.c[i] = h_mod_i128(m, c.primes[i]);
+        cv.sh[i] = h_shoup(cv.c[i], c.primes[i]);
+    }
+    return cv;
+}
+
+CtObj *ev_add_const(Ctx &c, const CtObj &a, double x)
+{
+    const __int128 m = h_round_away(x * a.scale);
+    CtObj *o = ct_new(c, a.level, a.scale);
+    k_add_scalar_c0(c, a, residues(c, m, a.level + 1), *o);
+    return o;
+}
+
+CtObj *ev_mul_int(Ctx &c, const CtObj &a, int64_t k)
+{
+    CtObj *o = ct_new(c, a.level, a.scale);
+    k_mul_scalar_ct(c, a, residues(c, (__int128)k, a.level + 1), *o);
+    return o;
+}
+
+CtObj *ev_rescale(Ctx &c, const CtObj &a)
+{
+    if (a.level < 1) throw_err(PPST_E_DEPTH, "rescale at level 0");
+    ensure_workspace(c);
+    CtObj *o = ct_new(c, a.level - 1, a.scale / (double)c.primes[a.level]);
+    k_rescale(c, a, *o);
+    return o;
+}
+
+CtObj *ev_mul_const(Ctx &c, const CtObj &a, double x, double target)
+{
+    if (a.level < 1) throw_err(PPST_E_DEPTH, "mul_const at level 0");
+    ensure_workspace(c);
+    const uint64_t ql = c.primes[a.level];
+    const double k = target > 0 ? x * (target / a.scale) : x;
+    const __int128 m = h_round_mul(k, ql);
+    CtObj *t = ct_new(c, a.level, a.scale);
+    CtObj *o = nullptr;
+    try {
+        k_mul_scalar_ct(c, a, residues(c, m, a.level + 1), *t);
+        o = ct_new(c, a.level - 1, target > 0 ? target : a.scale);
+        k_rescale(c, *t, *o);
+    } catch (...) {
+        ct_free(t);
+        ct_free(o);
+        throw;
+    }
+    ct_free(t);
+    return o;
+}
+
+CtObj *ev_drop(Ctx &c, const CtObj &a, int level)
+{
+    if (level > a.level || level < 0) throw_err(PPST_E_ARG, "drop: bad level");
+    CtObj *o = ct_new(c, level, a.scale);
+    const size_t ps = (size_t)(c.L + 1) * c.N;
+    k_copy(c, o->d, a.d, (size_t)(level + 1) * c.N);
+    k_copy(c, o->d + ps, a.d + ps, (size_t)(level + 1) * c.N);
+    return o;
+}
+
+// hybrid key switch of d (evaluation domain, limbs 0..level, held in ws_d2):
+// out_k = add_k + ModDown(sum_j ModUp_j(d) * key_j,k)
+static void key_switch(Ctx &c, int level, const Swk &key, const uint64_t *add0, const uint64_t *add1, uint64_t *out0,
+                       uint64_t *out1)
+{
+    ensure_workspace(c);
+    ntt_inv(c, map_poly(c, c.ws_d2, level));
+    k_modup(c, c.ws_d2, level, c.ws_ext);
+    LimbMap me{c.ws_ext, c.ext_rows() * c.N, level + 1 + c.K, c.ndigits(level), level + 1, 0, c.L + 1};
+    ntt_fwd(c, me);
+    k_inner_product(c, c.ws_ext, key, level, c.ws_acc);
+    k_moddown(c, c.ws_acc, level, add0, add1, out0, out1);
+}
+
+CtObj *ev_hmult(Ctx &c, const EvkObj &k, const CtObj &a, const CtObj &b)
+{
+    const int lv = std::min(a.level, b.level);
+    if (lv < 1) throw_err(PPST_E_DEPTH, "hmult at level 0");
+    if (!k.relin.d) throw_err(PPST_E_STATE, "no relinearisation key");
+    ensure_workspace(c);
+    CtObj *t = ct_new(c, lv, a.scale * b.scale);
+    CtObj *o = nullptr;
+    try {
+        k_tensor(c, a, b, lv, t->c0(), t->c1(), c.ws_d2);
+        key_switch(c, lv, k.relin, t->c0(), t->c1(), t->c0(), t->c1());
+        o = ct_new(c, lv - 1, (a.scale * b.scale) / (double)c.primes[lv]);
+        k_rescale(c, *t, *o);
+    } catch (...) {
+        ct_free(t);
+        ct_free(o);
+        throw;
+    }
+    ct_free(t);
+    return o;
+}
+
+CtObj *ev_rotate(Ctx &c, const EvkObj &k, const CtObj &a, int r)
+{
+    const int rr = ((r % c.S) + c.S) % c.S;
+    if (rr == 0) return ct_clone(a);
+    auto it = k.rot.find(rr);
+    if (it == k.rot.end()) throw_err(PPST_E_STATE, "no Galois key for rotation " + std::to_string(rr));
+    ensure_workspace(c);
+    const size_t ps = (size_t)(c.L + 1) * c.N;
+    CtObj *o = ct_new(c, a.level, a.scale);
+    try {
+        k_automorph(c, a.d, a.level, galois_elt(c, rr), o->d, ps, 2);
+        k_copy(c, c.ws_d2, o->c1(), (size_t)(a.level + 1) * c.N);
+        key_switch(c, a.level, it->second, o->c0(), nullptr, o->c0(), o->c1());
+    } catch (...) {
+        ct_free(o);
+        throw;
+    }
+    return o;
+}
+
+CtObj *ev_rotsum(Ctx &c, const EvkObj &k, const CtObj &a)
+{
+    CtObj *acc = ct_clone(a);
+    try {
+        for (int i = 0; i < c.logN - 1; i++) {
+            CtObj *r = ev_rotate(c, k, *acc, 1 << i);
+            CtObj *s = nullptr;
+            try {
+                s = ev_add(c, *acc, *r, false);
+            } catch (...) {
+                ct_free(r);
+                throw;
+            }
+            ct_free(r);
+            ct_free(acc);
+            acc = s;
+        }
+    } catch (...) {
+        ct_free(acc);
+        throw;
+    }
+    return acc;
+}
+
+}  // namespace ppst

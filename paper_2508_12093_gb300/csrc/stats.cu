@@ -1,0 +1,338 @@
+// stats.cu -- PP-STAT statistic programs over the GPU evaluator.
+//
+//  * CryptoInvSqrt(v, C) (Sec. 5, Alg. 2 with n = 2, Alg. 3, Eq. 1, Eq. 3):
+//    u = v - 1 (Eq. 1); y0 = degree 2^k - 1 Chebyshev interpolant of
+//    F(u, C) = 1 / (sqrt(C) sqrt(u + 1)) evaluated at u (Alg. 3 without
+//    bootstrapping); then t Newton steps y <- 1.5 y - x' y^3, x' = v C / 2
+//    (Alg. 2; the 1/n multiplier carries the constant C of Eq. 3).
+//  * CryptoSqrt(v, C) (Eq. 4): the interpolant of sqrt(C) sqrt(u + 1) alone.
+//  * Mean(x, B), Variance(x, B) with the 1/B constants folded into the
+//    plaintext multipliers (Sec. 6.1, Eq. 2): Variance costs depth 2.
+//  * ZNorm (Alg. 4), Kurt (Alg. 5), Skew (third-moment mirror of Alg. 5),
+//    CV (Alg. 6 for a positive mean, no Sign), PCC (Sec. 6.5).
+// Where the paper is silent: the Chebyshev sum is evaluated baby-step
+// giant-step in the Chebyshev basis (T_2i = 2 T_i^2 - 1, T_2i+1 = 2 T_i T_i+1
+// - T_1, giants T_2^m, recursive division by T_n); leaf sums steer every Mul(P)
+// to a common scale so that all Adds see equal scales; Newton's products are
+// associated (x' y)(y y) (depth 2 per step); padding slots of multi-ciphertext
+// columns are corrected with integer multiples of mu^p.
+#include <cmath>
+#include <functional>
+#include <map>
+#include <memory>
+
+#include "ctx.cuh"
+
+namespace ppst {
+
+namespace {
+
+struct Holder {
+    CtObj *ct;
+    explicit Holder(CtObj *p) : ct(p) {}
+    ~Holder()
+    {
+        if (ct) ct_free(ct);
+    }
+    CtObj *release()
+    {
+        CtObj *p = ct;
+        ct = nullptr;
+        return p;
+    }
+};
+typedef std::shared_ptr<Holder> H;
+
+struct Ev {
+    Ctx &c;
+    const EvkObj &k;
+    H w(CtObj *p) { return std::make_shared<Holder>(p); }
+    int level(const H &a) const { return a->ct->level; }
+    double scale(const H &a) const { return a->ct->scale; }
+    uint64_t prime(int l) const { return c.primes[l]; }
+    H add(const H &a, const H &b) { return w(ev_add(c, *a->ct, *b->ct, false)); }
+    H sub(const H &a, const H &b) { return w(ev_add(c, *a->ct, *b->ct, true)); }
+    H add_const(const H &a, double x) { return w(ev_add_const(c, *a->ct, x)); }
+    H mul_int(const H &a, int64_t m) { return w(ev_mul_int(c, *a->ct, m)); }
+    H mul_const(const H &a, double x, double target = 0) { return w(ev_mul_const(c, *a->ct, x, target)); }
+    H hmult(const H &a, const H &b) { return w(ev_hmult(c, k, *a->ct, *b->ct)); }
+    H drop(const H &a, int l) { return l == a->ct->level ? a : w(ev_drop(c, *a->ct, l)); }
+    H rotsum(const H &a) { return w(ev_rotsum(c, k, *a->ct)); }
+};
+
+// ---- Chebyshev interpolation (Sec. 3.4, Eq. 1, 3, 4) ----
+std::vector<double> cheb_coeffs(const std::function<double(double)> &F, int d)
+{
+    const int n = d + 1;
+    std::vector<double> th(n), f(n), c(n);
+    for (int j = 0; j < n; j++) th[j] = M_PI * (j + 0.5) / n;
+    for (int j = 0; j < n; j++) f[j] = F(std::cos(th[j]));
+    for (int k = 0; k < n; k++) {
+        double s = 0.0;
+        for (int j = 0; j < n; j++) s += f[j] * std::cos(k * th[j]);
+        c[k] = 2.0 * s / n;
+    }
+    c[0] *= 0.5;
+    return c;
+}
+
+std::function<double(double)> inv_sqrt_target(double C)
+{
+    return [C](double u) { return u > -1.0 ? 1.0 / (std::sqrt(C) * std::sqrt(u + 1.0)) : 0.0; };
+}
+
+std::function<double(double)> sqrt_target(double C)
+{
+    return [C](double u) { return u >= -1.0 ? std::sqrt(C) * std::sqrt(u + 1.0) : 0.0; };
+}
+
+// p = q T_n + r: q_0 = c_n, q_i = 2 c_{n+i}; r_0 = c_0, r_i = c_i - c_{2n-i}
+void cheb_split(const std::vector<double> &c, std::vector<double> &q, std::vector<double> &r)
+{
+    const size_t n = c.size() / 2;
+    q.assign(n, 0.0);
+    r.assign(n, 0.0);
+    q[0] = c[n];
+    r[0] = c[0];
+    for (size_t i = 1; i < n; i++) {
+        q[i] = 2.0 * c[n + i];
+        r[i] = c[i] - c[2 * n - i];
+    }
+}
+
+struct Cheb {
+    Ev &ev;
+    std::map<int, H> T;
+    int baby;
+
+    int rec_level(int len)
+    {
+        if (len <= baby) {
+            int lv = 1 << 30;
+            for (int i = 1; i < len; i++) lv = std::min(lv, ev.level(T[i]));
+            return lv - 1;
+        }
+        const int n = len / 2;
+        const int lq = std::min(rec_level(n), ev.level(T[n])) - 1;
+        return std::min(lq, rec_level(n));
+    }
+
+    H rec(const std::vector<double> &c, double target)
+    {
+        const int len = (int)c.size();
+        if (len <= baby) {
+            int lv = 1 << 30;
+            for (int i = 1; i < len; i++) lv = std::min(lv, ev.level(T[i]));
+            H acc;
+            for (int i = 1; i < len; i++) {
+                H term = ev.mul_const(ev.drop(T[i], lv), c[i], target);
+                acc = acc ? ev.add(acc, term) : term;
+            }
+            return ev.add_const(acc, c[0]);
+        }
+        const int n = len / 2;
+        std::vector<double> q, r;
+        cheb_split(c, q, r);
+        const int lvl = std::min(rec_level(n), ev.level(T[n]));
+        const double tq = target * (double)ev.prime(lvl) / ev.scale(T[n]);
+        H prod = ev.hmult(rec(q, tq), T[n]);
+        H rest = rec(r, ev.scale(prod));
+        return ev.add(prod, rest);
+    }
+};
+
+H cheb_eval(Ev &ev, const H &u, const std::vector<double> &c)
+{
+    int k = 0;
+    while ((1u << k) < c.size()) k++;
+    if ((1u << k) != c.size() || k < 1) throw_err(PPST_E_ARG, "Chebyshev length must be a power of two");
+    const int b = (k + 1) / 2;
+    Cheb ch{ev, {}, 1 << b};
+    ch.T[1] = u;
+    for (int i = 2; i <= (1 << b); i++) {
+        if (i % 2 == 0) {
+            const H &h = ch.T[i / 2];
+            ch.T[i] = ev.add_const(ev.mul_int(ev.hmult(h, h), 2), -1.0);
+        } else {
+            H p = ev.mul_int(ev.hmult(ch.T[(i - 1) / 2], ch.T[(i + 1) / 2]), 2);
+            H t1 = ev.mul_const(ev.drop(ch.T[1], ev.level(p) + 1), 1.0, ev.scale(p));
+            ch.T[i] = ev.sub(p, t1);
+        }
+    }
+    for (int m = b + 1; m < k; m++) {
+        const H &h = ch.T[1 << (m - 1)];
+        ch.T[1 << m] = ev.add_const(ev.mul_int(ev.hmult(h, h), 2), -1.0);
+    }
+    return ch.rec(c, ev.c.scale);
+}
+
+H crypto_inv_sqrt(Ev &ev, const H &v, double C, int k, int t)
+{
+    const std::vector<double> c = cheb_coeffs(inv_sqrt_target(C), (1 << k) - 1);
+    H y = cheb_eval(ev, ev.add_const(v, -1.0), c);
+    H xh = ev.mul_const(v, C / 2.0);
+    for (int it = 0; it < t; it++) {
+        H y2 = ev.hmult(y, y);
+        H xy = ev.hmult(xh, y);
+        H b = ev.hmult(xy, y2);
+        H a = ev.mul_const(ev.drop(y, ev.level(b) + 1), 1.5, ev.scale(b));
+        y = ev.sub(a, b);
+    }
+    return y;
+}
+
+H crypto_sqrt(Ev &ev, const H &v, double C, int k)
+{
+    return cheb_eval(ev, ev.add_const(v, -1.0), cheb_coeffs(sqrt_target(C), (1 << k) - 1));
+}
+
+typedef std::vector<H> Col;
+
+H col_sum(Ev &ev, const Col &x)
+{
+    H acc = x[0];
+    for (size_t i = 1; i < x.size(); i++) acc = ev.add(acc, x[i]);
+    return acc;
+}
+
+H variance(Ev &ev, const Col &x, size_t n, double B, const H &R)
+{
+    const double cst = 1.0 / (B * std::sqrt((double)n));
+    H acc;
+    for (const H &ct : x) {
+        H y = ev.mul_const(ct, cst);
+        H z = ev.hmult(y, y);
+        acc = acc ? ev.add(acc, z) : z;
+    }
+    H a = ev.rotsum(acc);
+    H m = ev.mul_const(R, 1.0 / (B * (double)n));
+    return ev.sub(a, ev.hmult(m, m));
+}
+
+H centred_power_sum(Ev &ev, const Col &x, const H &mu, int power)
+{
+    H acc;
+    for (const H &ct : x) {
+        H x1 = ev.sub(ct, mu);
+        H x2 = ev.hmult(x1, x1);
+        H xp = power == 4 ? ev.hmult(x2, x2) : ev.hmult(x2, x1);
+        acc = acc ? ev.add(acc, xp) : xp;
+    }
+    return ev.rotsum(acc);
+}
+
+Col znorm(Ev &ev, const Col &x, size_t n, double B, int k, int t)
+{
+    H R = ev.rotsum(col_sum(ev, x));
+    H mu = ev.mul_const(R, 1.0 / (double)n);
+    H inv = crypto_inv_sqrt(ev, variance(ev, x, n, B, R), B * B, k, t);
+    Col out;
+    for (const H &ct : x) out.push_back(ev.hmult(ev.sub(ct, mu), inv));
+    return out;
+}
+
+H kurt(Ev &ev, const Col &x, size_t n, double B, int k, int t)
+{
+    H R = ev.rotsum(col_sum(ev, x));
+    H mu = ev.mul_const(R, 1.0 / (double)n);
+    H X = centred_power_sum(ev, x, mu, 4);
+    const int64_t pads = (int64_t)(x.size() * (size_t)ev.c.S) - (int64_t)n;
+    if (pads) {
+        H mu2 = ev.hmult(mu, mu);
+        X = ev.sub(X, ev.mul_int(ev.hmult(mu2, mu2), pads));
+    }
+    H num = ev.mul_const(X, 1.0 / (double)n);
+    H inv = crypto_inv_sqrt(ev, variance(ev, x, n, B, R), B * B, k, t);
+    H inv2 = ev.hmult(inv, inv);
+    return ev.hmult(num, ev.hmult(inv2, inv2));
+}
+
+H skew(Ev &ev, const Col &x, size_t n, double B, int k, int t)
+{
+    H R = ev.rotsum(col_sum(ev, x));
+    H mu = ev.mul_const(R, 1.0 / (double)n);
+    H X = centred_power_sum(ev, x, mu, 3);
+    const int64_t pads = (int64_t)(x.size() * (size_t)ev.c.S) - (int64_t)n;
+    if (pads) {
+        H mu2 = ev.hmult(mu, mu);
+        X = ev.add(X, ev.mul_int(ev.hmult(mu2, mu), pads));
+    }
+    H num = ev.mul_const(X, 1.0 / (double)n);
+    H inv = crypto_inv_sqrt(ev, variance(ev, x, n, B, R), B * B, k, t);
+    H inv3 = ev.hmult(ev.hmult(inv, inv), inv);
+    return ev.hmult(num, inv3);
+}
+
+H cv(Ev &ev, const Col &x, size_t n, double B, int k, int t)
+{
+    H R = ev.rotsum(col_sum(ev, x));
+    H muB = ev.mul_const(R, 1.0 / (B * (double)n));
+    H isq = crypto_inv_sqrt(ev, muB, B, k, t);
+    H mu_inv = ev.hmult(isq, isq);
+    H std_ = crypto_sqrt(ev, variance(ev, x, n, B, R), B * B, k);
+    return ev.hmult(std_, mu_inv);
+}
+
+H pcc(Ev &ev, const Col &x, const Col &y, size_t n, double Bx, double By, int k, int t)
+{
+    H Rx = ev.rotsum(col_sum(ev, x));
+    H Ry = ev.rotsum(col_sum(ev, y));
+    H mux = ev.mul_const(Rx, 1.0 / (double)n);
+    H muy = ev.mul_const(Ry, 1.0 / (double)n);
+    H acc;
+    for (size_t i = 0; i < x.size(); i++) {
+        H p = ev.hmult(ev.sub(x[i], mux), ev.sub(y[i], muy));
+        acc = acc ? ev.add(acc, p) : p;
+    }
+    H Cs = ev.rotsum(acc);
+    const int64_t pads = (int64_t)(x.size() * (size_t)ev.c.S) - (int64_t)n;
+    if (pads) Cs = ev.sub(Cs, ev.mul_int(ev.hmult(mux, muy), pads));
+    H cov = ev.mul_const(Cs, 1.0 / (double)n);
+    H ix = crypto_inv_sqrt(ev, variance(ev, x, n, Bx, Rx), Bx * Bx, k, t);
+    H iy = crypto_inv_sqrt(ev, variance(ev, y, n, By, Ry), By * By, k, t);
+    return ev.hmult(ev.hmult(cov, ix), iy);
+}
+
+// non-owning handles around a column's ciphertexts
+Col view(const ColObj &col)
+{
+    Col out;
+    for (CtObj *ct : col.cts) {
+        auto h = std::shared_ptr<Holder>(new Holder(ct), [](Holder *p) {
+            p->ct = nullptr;  // the column keeps ownership
+            delete p;
+        });
+        out.push_back(h);
+    }
+    return out;
+}
+
+}  // namespace
+
+void run_queries(Ctx &c, const EvkObj &k, const std::vector<QueryIn> &qs, std::vector<ResObj *> &out)
+{
+    Ev ev{c, k};
+    for (const QueryIn &q : qs) {
+        const int kk = q.o.cheb_log2deg, tt = q.o.newton_steps;
+        Col x = view(*q.x);
+        const size_t n = q.x->n;
+        Col res;
+        switch (q.stat) {
+        case PPST_ZSCORE: res = znorm(ev, x, n, q.o.B_x, kk, tt); break;
+        case PPST_KURT: res.push_back(kurt(ev, x, n, q.o.B_x, kk, tt)); break;
+        case PPST_SKEW: res.push_back(skew(ev, x, n, q.o.B_x, kk, tt)); break;
+        case PPST_CV: res.push_back(cv(ev, x, n, q.o.B_x, kk, tt)); break;
+        case PPST_PCC: res.push_back(pcc(ev, x, view(*q.y), n, q.o.B_x, q.o.B_y, kk, tt)); break;
+        default: throw_err(PPST_E_ARG, "unknown statistic");
+        }
+        ResObj *r = new ResObj();
+        r->ctx = &c;
+        r->stat = q.stat;
+        r->n = n;
+        r->level_in = q.x->cts[0]->level;
+        for (H &h : res) r->cts.push_back(h->release());
+        out.push_back(r);
+    }
+}
+
+}  // namespace ppst

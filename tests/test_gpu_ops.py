@@ -1,0 +1,157 @@
+"""GPU parity of the evaluator ops, through the C ABI, against the oracle.
+
+Every comparison is bit-exact on coefficient-domain limbs: both sides derive
+their keys and noise from the same seeds (independent ChaCha20 streams) and
+the GPU imports the oracle's ciphertexts (encoding is FP64 and not bit-exact
+across two FFT implementations, so parity starts from shared ciphertexts).
+"""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+# N = 2^12, 6 Q primes (q0 60-bit, 40-bit), 2 special primes, 3 digits of 2
+SMALL = dict(log_n=12, n_q=6, n_p=2, dnum=3, q0_bits=60, q_bits=40, p_bits=60, log_scale=40)
+
+
+@pytest.fixture(scope="module")
+def env():
+    import paper_2508_12093_gb300 as pp
+    from oracle import ckks as ock
+    ctx = pp.Context(SMALL)
+    sk, evk = ctx.keygen(7)
+    oc = ock.Ckks(ock.Params(**SMALL))
+    ok = oc.keygen(7, rotations=[1 << i for i in range(SMALL["log_n"] - 1)])
+    return ctx, sk, evk, oc, ok
+
+
+def fresh(env, seed, lo=-1.0, hi=1.0):
+    ctx, sk, evk, oc, ok = env
+    x = workloads.uniform_column(oc.prm.S, seed=seed, lo=lo, hi=hi)
+    o = oc.encrypt_column(ok["pk"], x, seed)[0]
+    g = ctx.ct_import(o.c0, o.c1, o.level, o.scale)
+    return x, o, g
+
+
+def same(ctx, g, o):
+    c0, c1, lv, sc = ctx.ct_export(g)
+    assert lv == o.level, (lv, o.level)
+    assert sc == o.scale, (sc, o.scale)
+    assert np.array_equal(c0, o.c0), "c0 limbs differ"
+    assert np.array_equal(c1, o.c1), "c1 limbs differ"
+
+
+@pytest.mark.parametrize("name", ["toy12", "n16_d6", "n16_d3", "n16_d12"])
+def test_prime_chain_matches_oracle(name):
+    import paper_2508_12093_gb300 as pp
+    from oracle import ckks as ock
+    prm = workloads.PARAMS[name]
+    ctx = pp.Context(prm)
+    op = ock.Params(**prm)
+    assert ctx.primes == op.q + op.p
+
+
+def test_keys_match_oracle(env):
+    ctx, sk, evk, oc, ok = env
+    assert np.array_equal(ctx.sk_export(sk), ok["s"])
+    for j in range(len(ok["relin"].b)):
+        b, a = ctx.evk_export(evk, -1, j)
+        assert np.array_equal(a, ok["relin"].a[j]) and np.array_equal(b, ok["relin"].b[j]), j
+    for r in (1, 64, oc.prm.S // 2):
+        b, a = ctx.evk_export(evk, r, 1)
+        assert np.array_equal(a, ok["rot"][r].a[1]) and np.array_equal(b, ok["rot"][r].b[1]), r
+
+
+def test_encryption_matches_oracle(env):
+    ctx, sk, evk, oc, ok = env
+    x = workloads.uniform_column(oc.prm.S, seed=4)
+    m = oc.encode_ints(x, oc.prm.scale)
+    g = ctx.encrypt_ints(evk, np.array(m, dtype=np.int64), 9, 2, oc.prm.scale)
+    o = oc.encrypt_ints(ok["pk"], m, 9, 2)
+    same(ctx, g, o)
+
+
+def test_import_export_roundtrip(env):
+    ctx = env[0]
+    x, o, g = fresh(env, 11)
+    same(ctx, g, o)
+    d = ctx.drop(g, 2)
+    same(ctx, d, env[3].drop(o, 2))
+
+
+def test_elementwise_ops(env):
+    ctx, sk, evk, oc, ok = env
+    _, oa, ga = fresh(env, 12)
+    _, ob, gb = fresh(env, 13)
+    same(ctx, ctx.add(ga, gb), oc.add(oa, ob))
+    same(ctx, ctx.sub(ga, gb), oc.sub(oa, ob))
+    for c in (0.75, -1.0, 3.0e-9, 1e3):
+        same(ctx, ctx.add_const(ga, c), oc.add_const(oa, c))
+    for k in (2, -3, 12345, 0):
+        same(ctx, ctx.mul_int(ga, k), oc.mul_int(oa, k))
+    # mixed levels: the higher operand is dropped
+    same(ctx, ctx.add(ctx.drop(ga, 3), gb), oc.add(oc.drop(oa, 3), ob))
+
+
+def test_rescale_and_mul_const(env):
+    ctx, sk, evk, oc, ok = env
+    _, oa, ga = fresh(env, 14)
+    same(ctx, ctx.rescale(ga), oc.rescale(oa))
+    for c in (0.37, -1.5, 1.0 / 2048, 123.456, 1e-12):
+        same(ctx, ctx.mul_const(ga, c), oc.mul_const(oa, c))
+    tgt = oa.scale * (1 + 2.0 ** -25)
+    same(ctx, ctx.mul_const(ga, 0.5, tgt), oc.mul_const(oa, 0.5, tgt))
+    lo = oc.drop(oa, 1)
+    same(ctx, ctx.mul_const(ctx.drop(ga, 1), 0.9), oc.mul_const(lo, 0.9))
+
+
+def test_hmult_all_levels(env):
+    ctx, sk, evk, oc, ok = env
+    xa, oa, ga = fresh(env, 15)
+    xb, ob, gb = fresh(env, 16)
+    for lv in range(oc.prm.L, 0, -1):
+        o = oc.hmult(oc.drop(oa, lv), ob, ok)
+        g = ctx.hmult(evk, ctx.drop(ga, lv), gb)
+        same(ctx, g, o)
+    # square (same operand twice) and decrypted value
+    g = ctx.hmult(evk, ga, ga)
+    same(ctx, g, oc.hmult(oa, oa, ok))
+    assert np.abs(ctx.decrypt_ct(sk, g) - xa * xa).max() < 2.0 ** -20
+
+
+def test_rotations(env):
+    ctx, sk, evk, oc, ok = env
+    xa, oa, ga = fresh(env, 17)
+    for r in (1, 2, 64, oc.prm.S // 2):
+        same(ctx, ctx.rotate(evk, ga, r), oc.rotate(oa, r, ok))
+    low = oc.drop(oa, 2)
+    same(ctx, ctx.rotate(evk, ctx.drop(ga, 2), 8), oc.rotate(low, 8, ok))
+    rs = ctx.rotsum(evk, ga)
+    same(ctx, rs, oc.rotsum(oa, ok))
+    assert abs(ctx.decrypt_ct(sk, rs)[5] - xa.sum()) < 1e-5
+    assert np.abs(ctx.decrypt_ct(sk, ctx.rotate(evk, ga, 3 * 0 + 16)) - np.roll(xa, -16)).max() < 1e-6
+
+
+def test_error_codes(env):
+    import paper_2508_12093_gb300 as pp
+    ctx, sk, evk, oc, ok = env
+    _, oa, ga = fresh(env, 18)
+    low = ctx.drop(ga, 0)
+    with pytest.raises(pp.PpstError) as e:
+        ctx.hmult(evk, low, low)
+    assert e.value.code == -2
+    with pytest.raises(pp.PpstError) as e:
+        ctx.mul_const(low, 2.0)
+    assert e.value.code == -2
+    with pytest.raises(pp.PpstError) as e:
+        ctx.rotate(evk, ga, 3)             # no Galois key for 3
+    assert e.value.code == -8
+    other = ctx.mul_const(ga, 1.0, ga.scale * (1 + 2.0 ** -10))
+    with pytest.raises(pp.PpstError) as e:
+        ctx.add(ctx.drop(ga, other.level), other)
+    assert e.value.code == -3
+    with pytest.raises(pp.PpstError) as e:
+        ctx.drop(ga, 9)
+    assert e.value.code == -1
