@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark: encrypted-statistic queries per second at N = 2^16 on GB300.
+
+Workload (one "step"): the skewness, kurtosis and coefficient of variation of
+one encrypted 32,768-row column of lognormal(9, 0.9)/1000 values (an
+insurance-charges stand-in), N = 2^16, 24 x ~50-bit primes + 4 special primes,
+dnum = 6, scale 2^50, Chebyshev degree 2^7 - 1, 3 Newton steps, B = 20: three
+statistic queries through the C ABI, keys and the ciphertext resident in HBM.
+
+JSON line (rank 0): value = queries/s over all ranks (replicas); e2e = the
+same through host buffers (ciphertext upload, queries, decryption); roofline of
+the dominant kernel (CUDA events on the library's stream during the timed
+steps); HMult+KeySwitch microbenchmark; per-query latency percentiles; the
+CPU oracle as a reported baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+PARAMS = workloads.PARAMS["n16_d6"]
+STATS = ("skew", "kurt", "cv")
+OPTS = dict(B_x=20.0, cheb_log2deg=7, newton_steps=3)
+METRIC = "stat queries/s at N=2^16; HMult+KeySwitch µs & HBM roofline %; p50/p99 latency"
+WORKLOAD = ("N=2^16 (32768 slots), 24 Q primes (60+23x50 bit) + 4 special 60-bit primes, dnum=6, scale 2^50; "
+            "skewness + kurtosis + CV of one 32768-row lognormal(mu=9, sigma=0.9)/1000 column "
+            "(Chebyshev degree 127, 3 Newton steps, B=20)")
+# HMult + key switch at the top level, dnum = 6: two input ciphertexts
+# (2 x 2 x 24 limbs), the relinearisation key (6 x 2 x 28 limbs) and the output
+# (2 x 24 limbs) of 2^16 words each
+HMULT_BYTES = (2 * 2 * 24 + 6 * 2 * 28 + 2 * 24) * 65536 * 8
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    def __init__(self, gpu):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            parts = [s.strip() for s in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle as the CPU baseline (bounded sample, scaled by the op trace)
+# ---------------------------------------------------------------------------
+class _CountEv:
+    """Counts the evaluator ops of a schedule (noise-free simulator underneath),
+    with the limb count each op runs on."""
+
+    def __init__(self, sim, L):
+        self.sim, self.L = sim, L
+        self.work = {"hmult": 0.0, "rot": 0.0, "mulc": 0.0, "add": 0.0}
+
+    def __getattr__(self, name):
+        return getattr(self.sim, name)
+
+    def _w(self, kind, lv):
+        self.work[kind] += (lv + 1) / (self.L + 1)
+
+    def hmult(self, a, b):
+        self._w("hmult", min(a.level, b.level))
+        return self.sim.hmult(a, b)
+
+    def mul_const(self, a, x, target=None):
+        self._w("mulc", a.level)
+        return self.sim.mul_const(a, x, target)
+
+    def add(self, a, b):
+        self._w("add", min(a.level, b.level))
+        return self.sim.add(a, b)
+
+    def sub(self, a, b):
+        self._w("add", min(a.level, b.level))
+        return self.sim.sub(a, b)
+
+    def rotsum(self, a):
+        for _ in range(int(math.log2(self.sim.S))):
+            self._w("rot", a.level)
+            self._w("add", a.level)
+        return self.sim.rotsum(a)
+
+
+def step_op_work():
+    """Limb-weighted op counts of one step (3 queries), from the schedule itself."""
+    from oracle import ckks as ock
+    from oracle import stats as ost
+    prm = ock.Params(**PARAMS)
+    ev = _CountEv(ost.SimEv(prm.q, prm.scale, prm.S), prm.L)
+    x = workloads.lognormal_column(prm.S, seed=1)
+    for name in STATS:
+        f = {"skew": ost.skew, "kurt": ost.kurt, "cv": ost.cv}[name]
+        f(ev, [ev.encrypt(x)], prm.S, OPTS["B_x"], OPTS["cheb_log2deg"], OPTS["newton_steps"])
+    return ev.work
+
+
+class OracleSampler:
+    """Times the oracle's top-level HMult, rotation and Mul(P) at N = 2^16 and
+    converts them to queries/s with the step's limb-weighted op trace."""
+
+    def __init__(self):
+        from oracle import ckks as ock
+        self.c = ock.Ckks(ock.Params(**PARAMS))
+        self.keys = self.c.keygen(2, rotations=[1])
+        x = workloads.lognormal_column(self.c.prm.S, seed=1)
+        self.ct = self.c.encrypt_column(self.keys["pk"], x, 3)[0]
+        self.work = step_op_work()
+
+    def sample(self):
+        t = {}
+        t0 = time.perf_counter()
+        self.c.hmult(self.ct, self.ct, self.keys)
+        t["hmult"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        self.c.rotate(self.ct, 1, self.keys)
+        t["rot"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        self.c.mul_const(self.ct, 0.5)
+        t["mulc"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        self.c.add(self.ct, self.ct)
+        t["add"] = time.perf_counter() - t0
+        step_s = sum(self.work[k] * t[k] for k in t)
+        return len(STATS) / step_s, sum(t.values()), t
+
+    DESC = ("exact CPU oracle (Python + C, one thread): one top-level HMult+KeySwitch, rotation, Mul(P)+rescale "
+            "and Add at N=2^16 timed, scaled by the limb-weighted op counts of one step's schedule")
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    s = OracleSampler()
+    for _ in range(args.warmup):
+        s.sample()
+    vals, cpu_s = [], 0.0
+    for _ in range(args.steps):
+        v, dt, _ = s.sample()
+        vals.append(v)
+        cpu_s += dt
+    value = sum(vals) / len(vals)
+    ms_per_step = 1000.0 * len(STATS) / value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "queries_per_step": len(STATS)},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                             "sample": OracleSampler.DESC},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    import paper_2508_12093_gb300 as pp
+    from oracle import stats as ost   # FP64 plaintext references only (accuracy check)
+
+    ctx = pp.Context(PARAMS)
+    sk, evk = ctx.keygen(2)
+    x = workloads.lognormal_column(ctx.S, seed=1)
+    col = ctx.encrypt_column(evk, x, 3)
+
+    # accuracy of the step's results (untimed)
+    ref = ost.plain_stats(x)
+    max_rel = 0.0
+    for s in STATS:
+        v, rep = ctx.decrypt(sk, ctx.query(evk, s, col, opts=OPTS))
+        max_rel = max(max_rel, abs(v[0] / ref[s] - 1))
+
+    def step(lat=None):
+        out = []
+        for s in STATS:
+            if lat is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+            out.append(ctx.query(evk, s, col, opts=OPTS))
+            if lat is not None:
+                e1 = torch.cuda.Event(enable_timing=True)
+                e1.record()
+                lat.append((e0, e1))
+        return out
+
+    # which kernel class dominates one step
+    ctx.prof_start()
+    step()
+    ctx.prof_stop()
+    shares = {}
+    for k in ctx.prof_classes():
+        n, ms, u = ctx.prof_read(k, with_units=True)
+        shares[k] = ms
+    dom = max(shares, key=shares.get)
+    tot = sum(shares.values())
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = Clocks(local)
+    lat = []
+    l0 = ctx.launch_count()
+    ctx.prof_start(dom)
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    e_start.record()
+    for _ in range(args.steps):
+        step(lat)
+    e_end.record()
+    torch.cuda.synchronize()
+    ctx.prof_stop()
+    barrier()
+    clk = clocks.stop()
+    launches = ctx.launch_count() - l0
+    t_ms = e_start.elapsed_time(e_end)
+    if dist:
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    n_dom, ms_dom, units_dom = ctx.prof_read(dom, with_units=True)
+    queries = len(STATS) * args.steps * world
+    value = queries / (t_ms / 1000.0)
+    lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
+
+    # roofline of the dominant kernel: algorithmic bytes = one read and one
+    # write of every limb it processes (transform passes, elementwise kernels)
+    peak, peak_kind = peaks()
+    alg_bytes = units_dom * 2 * 8 * ctx.N
+    achieved = (alg_bytes / (ms_dom / 1000.0)) / 1e9 if ms_dom > 0 else None
+
+    # HMult + key switch microbenchmark (top level, dnum = 6)
+    a = ctx.encrypt_ints(evk, np.zeros(ctx.N, dtype=np.int64), 9, 0, ctx_scale(ctx))
+    for _ in range(5):
+        ctx.hmult(evk, a, a)
+    torch.cuda.synchronize()
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 50
+    h0.record()
+    for _ in range(reps):
+        ctx.hmult(evk, a, a)
+    h1.record()
+    torch.cuda.synchronize()
+    hmult_us = 1000.0 * h0.elapsed_time(h1) / reps
+    hmult_gbs = HMULT_BYTES / (hmult_us * 1e-6) / 1e9
+
+    # end to end through the public API with host buffers: the client's
+    # ciphertext (pinned host limbs) is uploaded, the three queries run, the
+    # results are decrypted on the host
+    c0, c1, lv, sc = ctx.ct_export(col_ct(ctx, col))
+    h_c0 = torch.from_numpy(c0).pin_memory()
+    h_c1 = torch.from_numpy(c1).pin_memory()
+    h2d = 2 * c0.nbytes
+    d2h = 0
+
+    def e2e_step():
+        nonlocal d2h
+        g = ctx.ct_import(h_c0.numpy(), h_c1.numpy(), lv, sc)
+        colg = ctx.col_from_cts([g], ctx.S)
+        res = [ctx.query(evk, s, colg, opts=OPTS) for s in STATS]
+        d = 0
+        for r in res:
+            v, rep = ctx.decrypt(sk, r)
+            d += (rep["level_out"] + 1) * ctx.N * 8
+        d2h = d
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, args.steps // 2)
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = len(STATS) * e2e_steps * world / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = OracleSampler()
+        v, dt, parts = s.sample()
+        cpu = {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
+               "sample": OracleSampler.DESC + f" ({dt:.1f} s of CPU work)",
+               "op_seconds": {k: round(t, 3) for k, t in parts.items()}}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "queries_per_step": len(STATS), "params": PARAMS,
+                       "l2": "inputs larger than L2: 2.8 GB of resident keys read every step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "accuracy": {"max_rel_err_vs_fp64": max_rel},
+            "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
+                                                                             int(0.99 * len(lat_ms)))],
+                           "mode": "one query at a time"},
+            "hmult_ks": {"us": hmult_us, "algorithmic_bytes": HMULT_BYTES, "achieved_gbs": hmult_gbs,
+                         "frac_of_hbm": hmult_gbs / peak},
+            "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if achieved else None, "traffic": None,
+                         "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                         else "fallback",
+                         "launches": n_dom, "avg_launch_us": 1000.0 * ms_dom / max(1, n_dom),
+                         "share_of_step": shares[dom] / tot,
+                         "algorithmic_bytes_per_launch": alg_bytes / max(1, n_dom)},
+            "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def ctx_scale(ctx):
+    return 2.0 ** ctx.params["log_scale"]
+
+
+def col_ct(ctx, col):
+    """The column's (single) ciphertext: what the client uploads."""
+    return col.cts()[0]
+
+
+if __name__ == "__main__":
+    main()

@@ -181,6 +181,10 @@ int ppst_res_ct(const ppst_res *res, uint32_t i, const ppst_ct **ct_out);
  * A column of n_rows values held by n_cts ciphertexts (copied). */
 int ppst_col_from_cts(ppst_ctx *ctx, const ppst_ct *const *cts, size_t n_cts, size_t n_rows,
                       ppst_col **out);
+/* Row and ciphertext counts of a column, and a view of its i-th ciphertext
+ * (owned by the column). */
+int ppst_col_info(const ppst_col *col, size_t *n_rows, uint32_t *n_cts);
+int ppst_col_ct(const ppst_col *col, uint32_t i, const ppst_ct **ct_out);
 
 /* ---- ciphertext ops (Add/Mul/Rot of Sec. 3.1) -------------------------------
  * import/export: coefficient-domain limbs, c0 and c1 each [level + 1][N].
@@ -225,6 +229,23 @@ int ppst_submit(ppst_server *srv, ppst_stat stat, const ppst_col *x, const ppst_
 int ppst_wait(ppst_server *srv, uint64_t ticket, int32_t timeout_ms, ppst_res **out);
 /* Latency of a finished ticket, in seconds from submit to result ready. */
 int ppst_ticket_latency(ppst_server *srv, uint64_t ticket, double *seconds);
+
+/* ---- kernel timing ----------------------------------------------------------
+ * While profiling is on, every launch of the named kernel class (NULL or "":
+ * every class) is bracketed by CUDA events on the context's stream. Classes:
+ * ntt_cols_fwd, ntt_chunks_fwd, ntt_chunks_inv, ntt_cols_inv, modup,
+ * inner_product, moddown_conv, moddown_final, rescale_bcast, rescale_final,
+ * tensor, automorph, elementwise, copy. ppst_prof_read synchronises, returns
+ * the launch count, summed device time and summed work units (limbs of N words
+ * for the transforms) of one class, and forgets them. ppst_prof_classes writes
+ * the recorded class names, comma separated. ppst_launch_count: kernels this
+ * context has launched so far (always counted, profiling on or off). */
+int ppst_prof_start(ppst_ctx *ctx, const char *kernel_class);
+int ppst_prof_stop(ppst_ctx *ctx);
+int ppst_prof_read(ppst_ctx *ctx, const char *kernel_class, uint64_t *launches, double *total_ms,
+                   uint64_t *units);
+int ppst_prof_classes(ppst_ctx *ctx, char *buf, size_t cap);
+int ppst_launch_count(const ppst_ctx *ctx, uint64_t *launches);
 
 /* Release any handle (ctx last). NULL is ignored. */
 void ppst_free(void *handle);

@@ -75,6 +75,16 @@ class Column(_Handle):
         super().__init__(ctx, ptr)
         self.n = n
 
+    def cts(self):
+        n = _lib.c_u32()
+        lib.ppst_col_info(self.ptr, None, ctypes.byref(n))
+        out = []
+        for i in range(n.value):
+            p = ctypes.c_void_p()
+            lib.ppst_col_ct(self.ptr, i, ctypes.byref(p))
+            out.append(_View(self.ctx, p.value, self))
+        return out
+
 
 class Result(_Handle):
     def cts(self):
@@ -302,6 +312,32 @@ class Context:
 
     def sync(self):
         self._check(lib.ppst_sync(self.ptr))
+
+    # -- kernel timing (CUDA events on the context's stream) ----------------------
+    def prof_start(self, kernel_class=None):
+        self._check(lib.ppst_prof_start(self.ptr, kernel_class.encode() if kernel_class else None))
+
+    def prof_stop(self):
+        self._check(lib.ppst_prof_stop(self.ptr))
+
+    def prof_classes(self):
+        buf = ctypes.create_string_buffer(4096)
+        self._check(lib.ppst_prof_classes(self.ptr, buf, 4096))
+        return [s for s in buf.value.decode().split(",") if s]
+
+    def prof_read(self, kernel_class, with_units=False):
+        n, ms, u = _lib.c_u64(), ctypes.c_double(), _lib.c_u64()
+        self._check(lib.ppst_prof_read(self.ptr, kernel_class.encode(), ctypes.byref(n), ctypes.byref(ms),
+                                       ctypes.byref(u)))
+        return (n.value, ms.value, u.value) if with_units else (n.value, ms.value)
+
+    def launch_count(self):
+        n = _lib.c_u64()
+        self._check(lib.ppst_launch_count(self.ptr, ctypes.byref(n)))
+        return n.value
+
+    def prof_read_all(self):
+        return {k: self.prof_read(k) for k in self.prof_classes()}
 
     def mem_info(self):
         a, b = ctypes.c_size_t(), ctypes.c_size_t()

@@ -65,6 +65,8 @@ SIGNATURES = {
     "ppst_res_count": (c_int, [c_void_p, u32p]),
     "ppst_res_ct": (c_int, [c_void_p, c_u32, PP]),
     "ppst_col_from_cts": (c_int, [c_void_p, PP, c_size_t, c_size_t, PP]),
+    "ppst_col_info": (c_int, [c_void_p, P(c_size_t), u32p]),
+    "ppst_col_ct": (c_int, [c_void_p, c_u32, PP]),
     "ppst_ct_import": (c_int, [c_void_p, u64p, u64p, c_u32, c_double, PP]),
     "ppst_ct_export": (c_int, [c_void_p, c_void_p, u64p, u64p, u32p, f64p]),
     "ppst_ct_level": (c_int, [c_void_p, u32p, f64p]),
@@ -82,6 +84,11 @@ SIGNATURES = {
     "ppst_submit": (c_int, [c_void_p, c_int, c_void_p, c_void_p, P(ppst_qopts), P(c_u64)]),
     "ppst_wait": (c_int, [c_void_p, c_u64, c_i32, PP]),
     "ppst_ticket_latency": (c_int, [c_void_p, c_u64, P(c_double)]),
+    "ppst_prof_start": (c_int, [c_void_p, ctypes.c_char_p]),
+    "ppst_prof_stop": (c_int, [c_void_p]),
+    "ppst_prof_read": (c_int, [c_void_p, ctypes.c_char_p, P(c_u64), P(ctypes.c_double), P(c_u64)]),
+    "ppst_launch_count": (c_int, [c_void_p, P(c_u64)]),
+    "ppst_prof_classes": (c_int, [c_void_p, ctypes.c_char_p, c_size_t]),
     "ppst_free": (None, [c_void_p]),
 }
 

@@ -344,6 +344,23 @@ int ppst_col_from_cts(ppst_ctx *ctx, const ppst_ct *const *cts, size_t n_cts, si
     });
 }
 
+int ppst_col_info(const ppst_col *col, size_t *n_rows, uint32_t *n_cts)
+{
+    const ColObj *c = (const ColObj *)col;
+    if (!ok(c, TAG_COL)) return PPST_E_ARG;
+    if (n_rows) *n_rows = c->n;
+    if (n_cts) *n_cts = (uint32_t)c->cts.size();
+    return PPST_OK;
+}
+
+int ppst_col_ct(const ppst_col *col, uint32_t i, const ppst_ct **ct_out)
+{
+    const ColObj *c = (const ColObj *)col;
+    if (!ok(c, TAG_COL) || !ct_out || i >= c->cts.size()) return PPST_E_ARG;
+    *ct_out = (const ppst_ct *)c->cts[i];
+    return PPST_OK;
+}
+
 int ppst_ct_import(ppst_ctx *ctx, const uint64_t *c0, const uint64_t *c1, uint32_t level, double scale,
                    ppst_ct **out)
 {
@@ -459,6 +476,72 @@ int ppst_mul_int(ppst_ctx *ctx, const ppst_ct *a, int64_t k, ppst_ct **out)
 int ppst_drop(ppst_ctx *ctx, const ppst_ct *a, uint32_t level, ppst_ct **out)
 {
     CT_OP(drop, { *out = (ppst_ct *)ev_drop(*c, *A, (int)level); })
+}
+
+int ppst_prof_start(ppst_ctx *ctx, const char *kernel_class)
+{
+    Ctx *c = (Ctx *)ctx;
+    if (!ok(c, TAG_CTX)) return PPST_E_ARG;
+    c->prof.on = true;
+    c->prof.only = kernel_class ? kernel_class : "";
+    return PPST_OK;
+}
+
+int ppst_prof_stop(ppst_ctx *ctx)
+{
+    Ctx *c = (Ctx *)ctx;
+    if (!ok(c, TAG_CTX)) return PPST_E_ARG;
+    c->prof.on = false;
+    return PPST_OK;
+}
+
+int ppst_prof_read(ppst_ctx *ctx, const char *kernel_class, uint64_t *launches, double *total_ms, uint64_t *units)
+{
+    Ctx *c = (Ctx *)ctx;
+    if (!ok(c, TAG_CTX) || !kernel_class) return PPST_E_ARG;
+    return guard(c, [&] {
+        PPST_CUDA(cudaStreamSynchronize(c->stream));
+        auto it = c->prof.rec.find(kernel_class);
+        uint64_t n = 0, u = 0;
+        double ms = 0;
+        if (it != c->prof.rec.end()) {
+            for (auto &pr : it->second) {
+                float t = 0;
+                PPST_CUDA(cudaEventElapsedTime(&t, pr.b, pr.e));
+                ms += t;
+                n++;
+                u += pr.units;
+                c->prof.spare.push_back(pr.b);
+                c->prof.spare.push_back(pr.e);
+            }
+            c->prof.rec.erase(it);
+        }
+        if (launches) *launches = n;
+        if (total_ms) *total_ms = ms;
+        if (units) *units = u;
+    });
+}
+
+int ppst_launch_count(const ppst_ctx *ctx, uint64_t *launches)
+{
+    const Ctx *c = (const Ctx *)ctx;
+    if (!ok(c, TAG_CTX) || !launches) return PPST_E_ARG;
+    *launches = c->prof.launches;
+    return PPST_OK;
+}
+
+int ppst_prof_classes(ppst_ctx *ctx, char *buf, size_t cap)
+{
+    Ctx *c = (Ctx *)ctx;
+    if (!ok(c, TAG_CTX) || !buf || !cap) return PPST_E_ARG;
+    std::string s;
+    for (auto &kv : c->prof.rec) {
+        if (!s.empty()) s += ",";
+        s += kv.first;
+    }
+    std::strncpy(buf, s.c_str(), cap - 1);
+    buf[cap - 1] = 0;
+    return PPST_OK;
 }
 
 void ppst_free(void *handle)

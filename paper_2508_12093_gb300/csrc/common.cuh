@@ -29,6 +29,11 @@ struct PrimeC {
     uint64_t w64;       // floor(2^64 / q): Shoup companion of 1, reduces a 64-bit word
 };
 
+// a twiddle and its Shoup companion, loaded as one 16-byte word
+struct __align__(16) Tw {
+    uint64_t w, s;
+};
+
 __host__ __device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t q) { return x >= q ? x - q : x; }
 
 __host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b)

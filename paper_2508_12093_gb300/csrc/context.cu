@@ -20,6 +20,35 @@ void check_launch(const char *what)
     if (e != cudaSuccess) throw_err(PPST_E_CUDA, std::string("launch ") + what + ": " + cudaGetErrorString(e));
 }
 
+cudaEvent_t Prof::take()
+{
+    if (!spare.empty()) {
+        cudaEvent_t e = spare.back();
+        spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    PPST_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+ProfScope::ProfScope(Ctx &cc, const char *k, uint64_t u) : c(cc), cls(k), units(u)
+{
+    c.prof.launches++;
+    if (c.prof.on && (c.prof.only.empty() || c.prof.only == cls)) {
+        b = c.prof.take();
+        PPST_CUDA(cudaEventRecord(b, c.stream));
+    }
+}
+
+ProfScope::~ProfScope()
+{
+    if (!b) return;
+    cudaEvent_t e = c.prof.take();
+    cudaEventRecord(e, c.stream);
+    c.prof.rec[cls].push_back(ProfRec{b, e, units});
+}
+
 // ---------------------------------------------------------------------------
 // host modular arithmetic (exact, 128-bit)
 // ---------------------------------------------------------------------------
@@ -346,7 +375,7 @@ Ctx *ctx_create(const ppst_params &pin, const ppst_allocator *alloc, cudaStream_
 
         // per-prime constants and transform tables
         c->hpc.resize(np);
-        std::vector<uint64_t> tw((size_t)np * N), twsh((size_t)np * N), itw((size_t)np * N), itwsh((size_t)np * N);
+        std::vector<Tw> twf((size_t)np * N), twi((size_t)np * N);
         std::vector<uint64_t> pw(N), ipw(N);
         for (int t = 0; t < np; t++) {
             const uint64_t qt = c->primes[t];
@@ -370,17 +399,13 @@ Ctx *ctx_create(const ppst_params &pin, const ppst_allocator *alloc, cudaStream_
             for (int k = 0; k < N; k++) {
                 const uint32_t r = brv((uint32_t)k, c->logN);
                 const size_t o = (size_t)t * N + k;
-                tw[o] = pw[r];
-                twsh[o] = h_shoup(pw[r], qt);
-                itw[o] = ipw[r];
-                itwsh[o] = h_shoup(ipw[r], qt);
+                twf[o] = Tw{pw[r], h_shoup(pw[r], qt)};
+                twi[o] = Tw{ipw[r], h_shoup(ipw[r], qt)};
             }
         }
         c->d_pc = upload(*c, c->hpc);
-        c->d_tw = upload(*c, tw);
-        c->d_tw_sh = upload(*c, twsh);
-        c->d_itw = upload(*c, itw);
-        c->d_itw_sh = upload(*c, itwsh);
+        c->d_twf = upload(*c, twf);
+        c->d_twi = upload(*c, twi);
 
         // discrete Gaussian CDT: T[k] = floor(2^64 P(|e| <= k)), IEEE double in this order
         {
@@ -492,7 +517,7 @@ void ctx_destroy(Ctx *c)
     // (sizes are only needed by user allocators; tables were taken with +256 slack)
     c->pool.trim();
     // device tables and workspace are not in the free lists; release them directly
-    std::vector<void *> own = {c->d_pc, c->d_tw, c->d_tw_sh, c->d_itw, c->d_itw_sh, c->d_cdt, c->d_ks,
+    std::vector<void *> own = {c->d_pc, c->d_twf, c->d_twi, c->d_cdt, c->d_ks,
                                c->ws_d2, c->ws_ext, c->ws_acc, c->ws_conv};
     for (void *p : own) {
         if (!p) continue;

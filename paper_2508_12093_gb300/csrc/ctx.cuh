@@ -87,8 +87,23 @@ struct HostPrime {
     uint64_t q, psi;
 };
 
+// per-kernel-class timing with CUDA events on the launching stream
+struct ProfRec {
+    cudaEvent_t b, e;
+    uint64_t units;  // work units of the launch (limbs for transforms and elementwise kernels)
+};
+struct Prof {
+    bool on = false;
+    std::string only;  // "" = every class
+    std::vector<cudaEvent_t> spare;
+    std::map<std::string, std::vector<ProfRec>> rec;
+    uint64_t launches = 0;  // kernel launches issued by this context (always counted)
+    cudaEvent_t take();
+};
+
 struct Ctx {
     uint32_t tag = TAG_CTX;
+    Prof prof;
     ppst_params prm{};
     int logN = 0, N = 0, S = 0, L = 0, K = 0, dnum = 0, alpha = 0, np = 0;
     double scale = 1.0, sigma = 3.2;
@@ -97,7 +112,7 @@ struct Ctx {
     std::vector<PrimeC> hpc;       // host copy of the per-prime constants
     std::vector<uint64_t> psi;
     PrimeC *d_pc = nullptr;
-    uint64_t *d_tw = nullptr, *d_tw_sh = nullptr, *d_itw = nullptr, *d_itw_sh = nullptr;
+    Tw *d_twf = nullptr, *d_twi = nullptr;  // [prime][N]: psi^brv(k), psi^-brv(k) with Shoup companions
     uint64_t *d_cdt = nullptr;  // discrete Gaussian CDT
     std::vector<uint64_t> cdt;
     // key-switching tables (device), offsets per (level, digit)
@@ -141,6 +156,16 @@ struct PpstError {
 void cuda_check(cudaError_t e, const char *what);
 #define PPST_CUDA(x) ::ppst::cuda_check((x), #x)
 void check_launch(const char *what);
+
+// brackets the launches of one kernel class with events when profiling is on
+struct ProfScope {
+    Ctx &c;
+    const char *cls;
+    uint64_t units;
+    cudaEvent_t b = nullptr;
+    ProfScope(Ctx &cc, const char *k, uint64_t u = 0);
+    ~ProfScope();
+};
 
 // ---- host math (host_math.cu) ----
 uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t q);

@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(EW_THREADS) k_ct_ew(const uint64_t *__restrict
 
 void k_add(Ctx &c, const CtObj &a, const CtObj &b, CtObj &out, bool sub)
 {
+    ProfScope _ps(c, "elementwise");
     const int nl = out.level + 1;
     ConstVec cv{};
     if (sub)
@@ -50,6 +51,7 @@ void k_add(Ctx &c, const CtObj &a, const CtObj &b, CtObj &out, bool sub)
 
 void k_neg(Ctx &c, const CtObj &a, CtObj &out)
 {
+    ProfScope _ps(c, "elementwise");
     const int nl = out.level + 1;
     ConstVec cv{};
     k_ct_ew<EW_NEG><<<ew_grid(c, 2 * nl), EW_THREADS, 0, c.stream>>>(a.d, nullptr, out.d, c.d_pc, cv, c.N, nl,
@@ -59,6 +61,7 @@ void k_neg(Ctx &c, const CtObj &a, CtObj &out)
 
 void k_mul_scalar_ct(Ctx &c, const CtObj &a, const ConstVec &cv, CtObj &out)
 {
+    ProfScope _ps(c, "elementwise");
     const int nl = out.level + 1;
     k_ct_ew<EW_MULC><<<ew_grid(c, 2 * nl), EW_THREADS, 0, c.stream>>>(a.d, nullptr, out.d, c.d_pc, cv, c.N, nl,
                                                                       (size_t)(c.L + 1) * c.N);
@@ -67,6 +70,7 @@ void k_mul_scalar_ct(Ctx &c, const CtObj &a, const ConstVec &cv, CtObj &out)
 
 void k_add_scalar_c0(Ctx &c, const CtObj &a, const ConstVec &cv, CtObj &out)
 {
+    ProfScope _ps(c, "elementwise");
     const int nl = out.level + 1;
     k_ct_ew<EW_ADDC0><<<ew_grid(c, 2 * nl), EW_THREADS, 0, c.stream>>>(a.d, nullptr, out.d, c.d_pc, cv, c.N, nl,
                                                                        (size_t)(c.L + 1) * c.N);
@@ -82,7 +86,10 @@ __global__ void k_copy_kernel(uint64_t *__restrict__ dst, const uint64_t *__rest
 void k_copy(Ctx &c, uint64_t *dst, const uint64_t *src, size_t words)
 {
     if (!words) return;
-    PPST_CUDA(cudaMemcpyAsync(dst, src, words * 8, cudaMemcpyDeviceToDevice, c.stream));
+    ProfScope _ps(c, "copy", words / c.N);
+    const size_t blocks = std::min<size_t>((words + 255) / 256, 4096);
+    k_copy_kernel<<<(unsigned)blocks, 256, 0, c.stream>>>(dst, src, words);
+    check_launch("k_copy");
 }
 
 // ---------------------------------------------------------------------------
@@ -110,6 +117,7 @@ __global__ void __launch_bounds__(EW_THREADS) k_tensor_kernel(const uint64_t *__
 
 void k_tensor(Ctx &c, const CtObj &a, const CtObj &b, int level, uint64_t *d0, uint64_t *d1, uint64_t *d2)
 {
+    ProfScope _ps(c, "tensor");
     k_tensor_kernel<<<ew_grid(c, level + 1), EW_THREADS, 0, c.stream>>>(a.d, b.d, d0, d1, d2, c.d_pc, c.N,
                                                                         (size_t)(c.L + 1) * c.N);
     check_launch("k_tensor");
@@ -166,6 +174,7 @@ __global__ void __launch_bounds__(EW_THREADS) k_modup_kernel(const uint64_t *__r
 
 void k_modup(Ctx &c, const uint64_t *d2coef, int level, uint64_t *ext)
 {
+    ProfScope _ps(c, "modup");
     const int nd = c.ndigits(level);
     DigitOffs offs;
     for (int j = 0; j < nd; j++) offs.off[j] = c.modup_off[level][j];
@@ -200,6 +209,7 @@ __global__ void __launch_bounds__(EW_THREADS) k_inner_kernel(const uint64_t *__r
 
 void k_inner_product(Ctx &c, const uint64_t *ext, const Swk &key, int level, uint64_t *acc)
 {
+    ProfScope _ps(c, "inner_product");
     const int E = level + 1 + c.K;
     k_inner_kernel<<<ew_grid(c, E), EW_THREADS, 0, c.stream>>>(ext, key.d, acc, c.d_pc, c.N, level, c.L, c.K,
                                                                c.ndigits(level), c.ext_rows() * c.N);
@@ -267,11 +277,15 @@ void k_moddown(Ctx &c, uint64_t *acc, int level, const uint64_t *add0, const uin
     // P rows of both accumulators to the coefficient domain
     LimbMap mp{acc + (size_t)(level + 1) * c.N, es, c.K, 2, 0, 0, c.L + 1};
     ntt_inv(c, mp);
-    k_moddown_conv_kernel<<<ew_grid(c, 2), EW_THREADS, 0, c.stream>>>(acc, c.ws_conv, c.d_ks + c.moddown_off, c.d_pc,
-                                                                      c.N, level, c.L, c.K, es, cs);
-    check_launch("k_moddown_conv");
+    {
+        ProfScope _ps(c, "moddown_conv");
+        k_moddown_conv_kernel<<<ew_grid(c, 2), EW_THREADS, 0, c.stream>>>(acc, c.ws_conv, c.d_ks + c.moddown_off,
+                                                                          c.d_pc, c.N, level, c.L, c.K, es, cs);
+        check_launch("k_moddown_conv");
+    }
     LimbMap mq{c.ws_conv, cs, level + 1, 2, level + 1, 0, 0};
     ntt_fwd(c, mq);
+    ProfScope _ps(c, "moddown_final");
     k_moddown_final_kernel<<<ew_grid(c, 2 * (level + 1)), EW_THREADS, 0, c.stream>>>(
         acc, c.ws_conv, add0, add1, out0, out1, c.d_pc, c.pinv, c.N, level + 1, es, cs);
     check_launch("k_moddown_final");
@@ -316,15 +330,19 @@ void k_rescale(Ctx &c, const CtObj &a, CtObj &out)
     const size_t ps = (size_t)(c.L + 1) * c.N;
     // top limb of c0 and c1 -> scratch rows [0], [1] of ws_d2, coefficient domain
     uint64_t *top = c.ws_d2;
-    PPST_CUDA(cudaMemcpyAsync(top, a.d + (size_t)l * c.N, c.N * 8, cudaMemcpyDeviceToDevice, c.stream));
-    PPST_CUDA(cudaMemcpyAsync(top + c.N, a.d + ps + (size_t)l * c.N, c.N * 8, cudaMemcpyDeviceToDevice, c.stream));
+    k_copy(c, top, a.d + (size_t)l * c.N, c.N);
+    k_copy(c, top + c.N, a.d + ps + (size_t)l * c.N, c.N);
     LimbMap mt{top, (size_t)c.N, 1, 2, 1, l, 0};
     ntt_inv(c, mt);
-    k_rescale_bcast_kernel<<<ew_grid(c, 2 * l), EW_THREADS, 0, c.stream>>>(top, c.ws_conv, c.d_pc, c.resc_qmodv[l],
-                                                                            c.N, l, ps);
-    check_launch("k_rescale_bcast");
+    {
+        ProfScope _ps(c, "rescale_bcast");
+        k_rescale_bcast_kernel<<<ew_grid(c, 2 * l), EW_THREADS, 0, c.stream>>>(top, c.ws_conv, c.d_pc,
+                                                                                c.resc_qmodv[l], c.N, l, ps);
+        check_launch("k_rescale_bcast");
+    }
     LimbMap mw{c.ws_conv, ps, l, 2, l, 0, 0};
     ntt_fwd(c, mw);
+    ProfScope _ps(c, "rescale_final");
     k_rescale_final_kernel<<<ew_grid(c, 2 * l), EW_THREADS, 0, c.stream>>>(a.d, c.ws_conv, out.d, c.d_pc, c.resc[l],
                                                                             c.N, l, ps);
     check_launch("k_rescale_final");
@@ -352,6 +370,7 @@ __global__ void __launch_bounds__(EW_THREADS) k_automorph_kernel(const uint64_t 
 
 void k_automorph(Ctx &c, const uint64_t *in, int level, uint64_t galois, uint64_t *out, size_t poly_stride, int npoly)
 {
+    ProfScope _ps(c, "automorph");
     k_automorph_kernel<<<ew_grid(c, npoly * (level + 1)), EW_THREADS, 0, c.stream>>>(in, out, c.logN, level + 1,
                                                                                       galois, poly_stride);
     check_launch("k_automorph");

@@ -134,6 +134,25 @@ def test_rotations(env):
     assert np.abs(ctx.decrypt_ct(sk, ctx.rotate(evk, ga, 3 * 0 + 16)) - np.roll(xa, -16)).max() < 1e-6
 
 
+@pytest.mark.parametrize("log_n", [10, 11, 13, 14, 15, 16])
+def test_every_ring_degree(log_n):
+    """Transform pass shapes for every supported N: import/export round trip,
+    HMult and one rotation, bit-exact against the oracle."""
+    import paper_2508_12093_gb300 as pp
+    from oracle import ckks as ock
+    prm = dict(log_n=log_n, n_q=3, n_p=1, dnum=3, q0_bits=60, q_bits=45, p_bits=60, log_scale=45)
+    ctx = pp.Context(prm)
+    sk, evk = ctx.keygen(3, rotations=[1])
+    oc = ock.Ckks(ock.Params(**prm))
+    ok = oc.keygen(3, rotations=[1])
+    x = workloads.uniform_column(oc.prm.S, seed=log_n)
+    o = oc.encrypt_column(ok["pk"], x, 4)[0]
+    g = ctx.ct_import(o.c0, o.c1, o.level, o.scale)
+    same(ctx, g, o)
+    same(ctx, ctx.hmult(evk, g, g), oc.hmult(o, o, ok))
+    same(ctx, ctx.rotate(evk, g, 1), oc.rotate(o, 1, ok))
+
+
 def test_error_codes(env):
     import paper_2508_12093_gb300 as pp
     ctx, sk, evk, oc, ok = env
