@@ -197,6 +197,21 @@ int ppst_ct_level(const ppst_ct *ct, uint32_t *level, double *scale);
 /* Mul(C): tensor, relinearise (hybrid key switch), add, rescale. */
 int ppst_hmult(ppst_ctx *ctx, const ppst_evk *evk, const ppst_ct *a, const ppst_ct *b,
                ppst_ct **out);
+/* Mul(C) that allocates no device memory (the paper has no counterpart: this
+ * serves callers that must not allocate once running, e.g. a host whose own
+ * allocator already holds all free HBM, or a latency-critical serving thread
+ * that cannot take cudaMalloc's device synchronisation). Same result as
+ * ppst_hmult, written into `out`, a ciphertext the caller already owns (any
+ * level; its contents, level and scale are replaced; it must not be a or b).
+ * Every temporary lives in one static 32 MiB device array that each GPU
+ * loading the library holds until exit; parameter sets needing more return
+ * PPST_E_ARG (N = 2^12 with 20 primes fits; N = 2^16 does not). The first
+ * call on a device looks up the array's address there (call it once before
+ * any stream capture). Calls share the array: calls whose GPU work overlaps
+ * race. It calls no device allocator: not cudaMalloc/cudaFree, not the
+ * context's pool, not the ppst_allocator. */
+int ppst_hmult_noalloc(ppst_ctx *ctx, const ppst_evk *evk, const ppst_ct *a, const ppst_ct *b,
+                       ppst_ct *out);
 /* Rot: slot j of the result = slot j + r of the input (Galois key needed). */
 int ppst_rotate(ppst_ctx *ctx, const ppst_evk *evk, const ppst_ct *a, int32_t r, ppst_ct **out);
 /* Rotate-and-sum over all N/2 slots (every slot = the total). */

@@ -283,6 +283,11 @@ class Context:
     def hmult(self, evk, a, b):
         return self._new(lib.ppst_hmult, evk.ptr, a.ptr, b.ptr)
 
+    def hmult_noalloc(self, evk, a, b, out):
+        """ppst_hmult_noalloc: writes a * b into the caller-owned ciphertext `out`."""
+        self._check(lib.ppst_hmult_noalloc(self.ptr, evk.ptr, a.ptr, b.ptr, out.ptr))
+        return out
+
     def rotate(self, evk, a, r):
         return self._new(lib.ppst_rotate, evk.ptr, a.ptr, r)
 

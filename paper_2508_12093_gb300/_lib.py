@@ -71,6 +71,7 @@ SIGNATURES = {
     "ppst_ct_export": (c_int, [c_void_p, c_void_p, u64p, u64p, u32p, f64p]),
     "ppst_ct_level": (c_int, [c_void_p, u32p, f64p]),
     "ppst_hmult": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, PP]),
+    "ppst_hmult_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ppst_rotate": (c_int, [c_void_p, c_void_p, c_void_p, c_i32, PP]),
     "ppst_rotsum": (c_int, [c_void_p, c_void_p, c_void_p, PP]),
     "ppst_rescale": (c_int, [c_void_p, c_void_p, PP]),
