@@ -118,6 +118,12 @@ class _CountEv:
         self._w("mulc", a.level)
         return self.sim.mul_const(a, x, target)
 
+    def lin_comb(self, cts, coeffs, target):
+        self._w("mulc", cts[0].level)          # one rescale
+        for _ in cts:
+            self._w("add", cts[0].level)       # one scalar multiply-add per term
+        return self.sim.lin_comb(cts, coeffs, target)
+
     def add(self, a, b):
         self._w("add", min(a.level, b.level))
         return self.sim.add(a, b)

@@ -225,6 +225,11 @@ int ppst_add_const(ppst_ctx *ctx, const ppst_ct *a, double c, ppst_ct **out);
  * c * (target / scale); the result's scale is target (or the input scale). */
 int ppst_mul_const(ppst_ctx *ctx, const ppst_ct *a, double c, double target, ppst_ct **out);
 int ppst_mul_int(ppst_ctx *ctx, const ppst_ct *a, int64_t k, ppst_ct **out);
+/* sum_k c_k a_k for 1..32 ciphertexts at one level: integer weights
+ * round(c_k (target / scale_k) q_l) (exact, ties away from zero), one rescale;
+ * the result's scale is `target`. The Chebyshev leaf sums of Alg. 3. */
+int ppst_lin_comb(ppst_ctx *ctx, const ppst_ct *const *cts, const double *coeffs, size_t n, double target,
+                  ppst_ct **out);
 /* Keep limbs 0..level. */
 int ppst_drop(ppst_ctx *ctx, const ppst_ct *a, uint32_t level, ppst_ct **out);
 

@@ -494,6 +494,29 @@ class Ckks:
         out.scale = tgt
         return out
 
+    def lin_comb(self, cts, coeffs, target_scale):
+        """sum_i c_i ct_i with one rescale: the integers m_i = round(k_i q_l),
+        k_i = c_i * (target / scale_i) in FP64 (exact product, ties away from
+        zero), multiply ciphertexts that share the level l; the sum is rescaled
+        once and its scale is exactly `target`."""
+        lv = cts[0].level
+        if any(ct.level != lv for ct in cts):
+            raise ValueError("lin_comb: operands at different levels")
+        if lv == 0:
+            raise DepthError("lin_comb at level 0")
+        ql = self.primes[lv]
+        idx = list(range(lv + 1))
+        acc0 = np.zeros((lv + 1, self.N), dtype=np.uint64)
+        acc1 = np.zeros_like(acc0)
+        for ct, c in zip(cts, coeffs):
+            k = float(c) * (float(target_scale) / ct.scale)
+            t = self.mul_int(ct, round_half_away(Fraction(k) * ql))
+            acc0 = self.vadd(acc0, t.c0, idx)
+            acc1 = self.vadd(acc1, t.c1, idx)
+        out = self.rescale(Ct(acc0, acc1, lv, target_scale))
+        out.scale = float(target_scale)
+        return out
+
     def tensor(self, a, b):
         idx = list(range(a.level + 1))
         d0 = self.polymul(a.c0, b.c0, idx)

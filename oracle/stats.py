@@ -17,8 +17,9 @@ TEST INFRASTRUCTURE (oracle). The schedules here follow the paper:
 Readings where the paper is silent (the same on the GPU side):
 * Chebyshev evaluation is baby-step giant-step in the Chebyshev basis with
   T_{2i} = 2 T_i^2 - 1, T_{2i+1} = 2 T_i T_{i+1} - T_1, giant steps T_{2^m}
-  and recursive division p = q T_n + r; leaf sums use Mul(P) with the scale
-  steered to a target so every Add sees equal scales.
+  and recursive division p = q T_n + r; a leaf sum sum_i c_i T_i is one
+  linear combination with integer weights round(c_i q_l) and a single rescale,
+  its scale steered to a target so every Add sees equal scales.
 * Newton's three products are associated as (x' y)(y y): same products as
   Alg. 2, depth 2 per step instead of 3.
 * Columns longer than one ciphertext are summed before one rotate-and-sum;
@@ -107,10 +108,7 @@ def _rec_level(ev, T, length, baby):
 def _cheb_rec(ev, T, c, baby, target):
     if len(c) <= baby:
         lv = min(ev.level(T[i]) for i in range(1, len(c)))
-        acc = None
-        for i in range(1, len(c)):
-            term = ev.mul_const(ev.drop(T[i], lv), c[i], target)
-            acc = term if acc is None else ev.add(acc, term)
+        acc = ev.lin_comb([ev.drop(T[i], lv) for i in range(1, len(c))], c[1:], target)
         return ev.add_const(acc, c[0])
     n = len(c) // 2
     q, r = cheb_split(c)
@@ -299,6 +297,9 @@ class CkksEv:
     def mul_const(self, a, x, target=None):
         return self._t(self.c.mul_const(a, x, target))
 
+    def lin_comb(self, cts, coeffs, target):
+        return self._t(self.c.lin_comb(cts, coeffs, target))
+
     def hmult(self, a, b):
         return self._t(self.c.hmult(a, b, self.keys))
 
@@ -363,6 +364,15 @@ class SimEv:
     def mul_const(self, a, x, target=None):
         self._need(a.level - 1)
         return SimCt(a.v * x, a.level - 1, a.scale if target is None else target)
+
+    def lin_comb(self, cts, coeffs, target):
+        lv = cts[0].level
+        assert all(c.level == lv for c in cts)
+        self._need(lv - 1)
+        v = np.zeros(self.S)
+        for ct, x in zip(cts, coeffs):
+            v = v + ct.v * x
+        return SimCt(v, lv - 1, target)
 
     def hmult(self, a, b):
         lv = min(a.level, b.level)

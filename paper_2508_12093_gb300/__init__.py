@@ -312,6 +312,11 @@ class Context:
     def mul_int(self, a, k):
         return self._new(lib.ppst_mul_int, a.ptr, int(k))
 
+    def lin_comb(self, cts, coeffs, target):
+        arr = (ctypes.c_void_p * len(cts))(*[c.ptr for c in cts])
+        cs = np.ascontiguousarray(coeffs, dtype=np.float64)
+        return self._new(lib.ppst_lin_comb, arr, cs.ctypes.data_as(_lib.f64p), len(cts), float(target))
+
     def drop(self, a, level):
         return self._new(lib.ppst_drop, a.ptr, level)
 

@@ -81,6 +81,7 @@ SIGNATURES = {
     "ppst_mul_const": (c_int, [c_void_p, c_void_p, c_double, c_double, PP]),
     "ppst_mul_int": (c_int, [c_void_p, c_void_p, c_i64, PP]),
     "ppst_drop": (c_int, [c_void_p, c_void_p, c_u32, PP]),
+    "ppst_lin_comb": (c_int, [c_void_p, PP, f64p, c_size_t, c_double, PP]),
     "ppst_server_create": (c_int, [c_void_p, c_void_p, c_size_t, c_u32, PP]),
     "ppst_submit": (c_int, [c_void_p, c_int, c_void_p, c_void_p, P(ppst_qopts), P(c_u64)]),
     "ppst_wait": (c_int, [c_void_p, c_u64, c_i32, PP]),

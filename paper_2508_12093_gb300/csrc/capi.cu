@@ -473,6 +473,26 @@ int ppst_mul_int(ppst_ctx *ctx, const ppst_ct *a, int64_t k, ppst_ct **out)
     CT_OP(mul_int, { *out = (ppst_ct *)ev_mul_int(*c, *A, k); })
 }
 
+int ppst_lin_comb(ppst_ctx *ctx, const ppst_ct *const *cts, const double *coeffs, size_t n, double target,
+                  ppst_ct **out)
+{
+    Ctx *c = (Ctx *)ctx;
+    if (!ok(c, TAG_CTX)) return PPST_E_ARG;
+    if (!out) return c->fail(PPST_E_ARG, "null output");
+    *out = nullptr;
+    return guard(c, [&] {
+        REQ(cts && coeffs && n >= 1 && n <= (size_t)LinArgs::MAXT, "bad arguments");
+        std::vector<const CtObj *> v;
+        std::vector<double> cs(coeffs, coeffs + n);
+        for (size_t i = 0; i < n; i++) {
+            const CtObj *A = (const CtObj *)cts[i];
+            REQ(ok(A, TAG_CT) && A->ctx == c, "bad ciphertext");
+            v.push_back(A);
+        }
+        *out = (ppst_ct *)ev_lin_comb(*c, v, cs, target);
+    });
+}
+
 int ppst_drop(ppst_ctx *ctx, const ppst_ct *a, uint32_t level, ppst_ct **out)
 {
     CT_OP(drop, { *out = (ppst_ct *)ev_drop(*c, *A, (int)level); })

@@ -209,7 +209,11 @@ CtObj *ct_new(Ctx &c, int level, double scale)
     ct->level = level;
     ct->scale = scale;
     try {
-        ct->d = (uint64_t *)c.pool.get(c.ct_words() * 8);
+        const size_t bytes = c.ct_words() * 8;
+        uint64_t *p = (uint64_t *)c.pool.get(bytes);
+        Ctx *cp = &c;
+        ct->buf = std::shared_ptr<uint64_t>(p, [cp, bytes](uint64_t *q) { cp->pool.put(q, bytes); });
+        ct->d = p;
     } catch (...) {
         delete ct;
         throw;
@@ -220,20 +224,23 @@ CtObj *ct_new(Ctx &c, int level, double scale)
 void ct_free(CtObj *ct)
 {
     if (!ct) return;
-    ct->ctx->pool.put(ct->d, ct->ctx->ct_words() * 8);
+    ct->buf.reset();
     ct->tag = TAG_DEAD;
     delete ct;
 }
 
-CtObj *ct_clone(const CtObj &a)
+CtObj *ct_view(const CtObj &a, int level)
 {
-    Ctx &c = *a.ctx;
-    CtObj *o = ct_new(c, a.level, a.scale);
-    const size_t ps = (size_t)(c.L + 1) * c.N;
-    k_copy(c, o->d, a.d, (size_t)(a.level + 1) * c.N);
-    k_copy(c, o->d + ps, a.d + ps, (size_t)(a.level + 1) * c.N);
+    CtObj *o = new CtObj();
+    o->ctx = a.ctx;
+    o->buf = a.buf;
+    o->d = a.d;
+    o->level = level;
+    o->scale = a.scale;
     return o;
 }
+
+CtObj *ct_clone(const CtObj &a) { return ct_view(a, a.level); }
 
 LimbMap map_ct(const Ctx &c, uint64_t *d, int level)
 {

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -37,9 +38,12 @@ struct Pool {
 
 struct Ctx;
 
+// Ciphertexts are immutable once written: every op writes a new buffer, so a
+// lower-level view (a "drop") can share its parent's buffer.
 struct CtObj {
     uint32_t tag = TAG_CT;
     Ctx *ctx = nullptr;
+    std::shared_ptr<uint64_t> buf;  // owner of the device buffer (shared by views)
     uint64_t *d = nullptr;  // [2][L+1][N], evaluation (NTT) domain, limbs 0..level valid
     int level = 0;
     double scale = 1.0;
@@ -185,7 +189,8 @@ void ctx_destroy(Ctx *c);
 void ensure_workspace(Ctx &c);
 CtObj *ct_new(Ctx &c, int level, double scale);
 void ct_free(CtObj *ct);
-CtObj *ct_clone(const CtObj &a);
+CtObj *ct_clone(const CtObj &a);             // a view of the same buffer and level
+CtObj *ct_view(const CtObj &a, int level);   // a view of limbs 0..level
 
 // ---- NTT (ntt.cu) ----
 void ntt_fwd(Ctx &c, const LimbMap &m);
@@ -204,6 +209,15 @@ void k_inner_product(Ctx &c, const uint64_t *ext, const Swk &key, int level, uin
 void k_moddown(Ctx &c, uint64_t *acc, int level, const uint64_t *add0, const uint64_t *add1, uint64_t *out0,
                uint64_t *out1);
 void k_rescale(Ctx &c, const CtObj &a, CtObj &out);
+// rescale of (a times the per-limb constants mul), without materialising the product
+void k_rescale_mul(Ctx &c, const CtObj &a, const ConstVec *mul, CtObj &out);
+struct LinArgs {
+    static constexpr int MAXT = 32;
+    const uint64_t *p[MAXT];
+    __int128 m[MAXT];
+    int n;
+};
+void k_lincomb(Ctx &c, const LinArgs &args, int level, CtObj &out);
 void k_automorph(Ctx &c, const uint64_t *in, int level, uint64_t galois, uint64_t *out, size_t poly_stride,
                  int npoly);
 void k_copy(Ctx &c, uint64_t *dst, const uint64_t *src, size_t words);
@@ -225,6 +239,8 @@ CtObj *ev_add_const(Ctx &c, const CtObj &a, double x);
 CtObj *ev_mul_int(Ctx &c, const CtObj &a, int64_t k);
 CtObj *ev_mul_const(Ctx &c, const CtObj &a, double x, double target);  // target <= 0: keep scale
 CtObj *ev_rescale(Ctx &c, const CtObj &a);
+// sum_k c_k a_k with integer weights round(c_k (target / scale_k) q_l) and one rescale
+CtObj *ev_lin_comb(Ctx &c, const std::vector<const CtObj *> &cts, const std::vector<double> &coeffs, double target);
 CtObj *ev_hmult(Ctx &c, const EvkObj &k, const CtObj &a, const CtObj &b);
 CtObj *ev_rotate(Ctx &c, const EvkObj &k, const CtObj &a, int r);
 CtObj *ev_rotsum(Ctx &c, const EvkObj &k, const CtObj &a);

@@ -72,11 +72,39 @@ CtObj *ev_mul_const(Ctx &c, const CtObj &a, double x, double target)
     const uint64_t ql = c.primes[a.level];
     const double k = target > 0 ? x * (target / a.scale) : x;
     const __int128 m = h_round_mul(k, ql);
-    CtObj *t = ct_new(c, a.level, a.scale);
+    const ConstVec mv = residues(c, m, a.level + 1);
+    CtObj *o = ct_new(c, a.level - 1, target > 0 ? target : a.scale);
+    try {
+        k_rescale_mul(c, a, &mv, *o);
+    } catch (...) {
+        ct_free(o);
+        throw;
+    }
+    return o;
+}
+
+CtObj *ev_lin_comb(Ctx &c, const std::vector<const CtObj *> &cts, const std::vector<double> &coeffs, double target)
+{
+    if (cts.empty() || cts.size() != coeffs.size() || cts.size() > (size_t)LinArgs::MAXT)
+        throw_err(PPST_E_ARG, "lin_comb: 1 to 32 terms");
+    const int lv = cts[0]->level;
+    for (const CtObj *t : cts)
+        if (t->level != lv) throw_err(PPST_E_ARG, "lin_comb: operands at different levels");
+    if (lv < 1) throw_err(PPST_E_DEPTH, "lin_comb at level 0");
+    if (!(target > 0)) throw_err(PPST_E_ARG, "lin_comb: target scale must be positive");
+    ensure_workspace(c);
+    const uint64_t ql = c.primes[lv];
+    LinArgs args;
+    args.n = (int)cts.size();
+    for (int k = 0; k < args.n; k++) {
+        args.p[k] = cts[k]->d;
+        args.m[k] = h_round_mul(coeffs[k] * (target / cts[k]->scale), ql);
+    }
+    CtObj *t = ct_new(c, lv, target);
     CtObj *o = nullptr;
     try {
-        k_mul_scalar_ct(c, a, residues(c, m, a.level + 1), *t);
-        o = ct_new(c, a.level - 1, target > 0 ? target : a.scale);
+        k_lincomb(c, args, lv, *t);
+        o = ct_new(c, lv - 1, target);
         k_rescale(c, *t, *o);
     } catch (...) {
         ct_free(t);
@@ -89,12 +117,9 @@ CtObj *ev_mul_const(Ctx &c, const CtObj &a, double x, double target)
 
 CtObj *ev_drop(Ctx &c, const CtObj &a, int level)
 {
+    (void)c;
     if (level > a.level || level < 0) throw_err(PPST_E_ARG, "drop: bad level");
-    CtObj *o = ct_new(c, level, a.scale);
-    const size_t ps = (size_t)(c.L + 1) * c.N;
-    k_copy(c, o->d, a.d, (size_t)(level + 1) * c.N);
-    k_copy(c, o->d + ps, a.d + ps, (size_t)(level + 1) * c.N);
-    return o;
+    return ct_view(a, level);
 }
 
 // hybrid key switch of d (evaluation domain, limbs 0..level, held in ws_d2):

@@ -310,28 +310,49 @@ __global__ void __launch_bounds__(EW_THREADS) k_rescale_bcast_kernel(const uint6
     w[(size_t)k * wstride + (size_t)i * N + c] = r;
 }
 
+// out_i = (c_i m_i - w_i) q_l^-1 = c_i (m_i q_l^-1) - w_i q_l^-1 (m_i = 1 for a plain rescale)
 __global__ void __launch_bounds__(EW_THREADS) k_rescale_final_kernel(const uint64_t *__restrict__ a,
                                                                      const uint64_t *__restrict__ w,
                                                                      uint64_t *__restrict__ out,
                                                                      const PrimeC *__restrict__ pc, ConstVec qlinv,
-                                                                     int N, int nl, size_t pstride)
+                                                                     ConstVec mq, int N, int nl, size_t pstride)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     const int row = blockIdx.y, k = row / nl, i = row - k * nl;
     const uint64_t q = pc[i].q;
     const size_t o = (size_t)k * pstride + (size_t)i * N + c;
-    out[o] = csub(shoup(sub_mod(a[o], w[o], q), qlinv.c[i], qlinv.sh[i], q), q);
+    const uint64_t x = csub(shoup(a[o], mq.c[i], mq.sh[i], q), q);
+    const uint64_t y = csub(shoup(w[o], qlinv.c[i], qlinv.sh[i], q), q);
+    out[o] = sub_mod(x, y, q);
 }
 
-void k_rescale(Ctx &c, const CtObj &a, CtObj &out)
+// top limb of both polynomials, times m (Shoup), into a scratch pair of rows
+__global__ void __launch_bounds__(EW_THREADS) k_top_copy_kernel(const uint64_t *__restrict__ a,
+                                                                uint64_t *__restrict__ top, uint64_t q, uint64_t m,
+                                                                uint64_t msh, int N, size_t off0, size_t off1)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int k = blockIdx.y;
+    const uint64_t v = a[(k ? off1 : off0) + c];
+    top[(size_t)k * N + c] = csub(shoup(v, m, msh, q), q);
+}
+
+void k_rescale_mul(Ctx &c, const CtObj &a, const ConstVec *mul, CtObj &out)
 {
     const int l = a.level;
     const size_t ps = (size_t)(c.L + 1) * c.N;
-    // top limb of c0 and c1 -> scratch rows [0], [1] of ws_d2, coefficient domain
+    const uint64_t ql = c.primes[l];
+    // top limb of c0 and c1 (times m_l) -> scratch rows [0], [1] of ws_d2, to the coefficient domain
     uint64_t *top = c.ws_d2;
-    k_copy(c, top, a.d + (size_t)l * c.N, c.N);
-    k_copy(c, top + c.N, a.d + ps + (size_t)l * c.N, c.N);
+    {
+        ProfScope _ps(c, "copy", 2);
+        const uint64_t m = mul ? mul->c[l] : 1, msh = mul ? mul->sh[l] : h_shoup(1, ql);
+        k_top_copy_kernel<<<ew_grid(c, 2), EW_THREADS, 0, c.stream>>>(a.d, top, ql, m, msh, c.N,
+                                                                        (size_t)l * c.N, ps + (size_t)l * c.N);
+        check_launch("k_top_copy");
+    }
     LimbMap mt{top, (size_t)c.N, 1, 2, 1, l, 0};
     ntt_inv(c, mt);
     {
@@ -342,10 +363,53 @@ void k_rescale(Ctx &c, const CtObj &a, CtObj &out)
     }
     LimbMap mw{c.ws_conv, ps, l, 2, l, 0, 0};
     ntt_fwd(c, mw);
-    ProfScope _ps(c, "rescale_final");
+    ConstVec mq;
+    for (int i = 0; i < l; i++) {
+        const uint64_t qi = c.primes[i];
+        mq.c[i] = mul ? h_mulmod(mul->c[i], c.resc[l].c[i], qi) : c.resc[l].c[i];
+        mq.sh[i] = h_shoup(mq.c[i], qi);
+    }
+    ProfScope _ps(c, "rescale_final", 2 * l);
     k_rescale_final_kernel<<<ew_grid(c, 2 * l), EW_THREADS, 0, c.stream>>>(a.d, c.ws_conv, out.d, c.d_pc, c.resc[l],
-                                                                            c.N, l, ps);
+                                                                            mq, c.N, l, ps);
     check_launch("k_rescale_final");
+}
+
+void k_rescale(Ctx &c, const CtObj &a, CtObj &out) { k_rescale_mul(c, a, nullptr, out); }
+
+// ---------------------------------------------------------------------------
+// linear combination with integer weights: out = sum_k m_k ct_k (one level)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(EW_THREADS) k_lincomb_kernel(LinArgs args, uint64_t *__restrict__ out,
+                                                               const PrimeC *__restrict__ pc, int N, int nl,
+                                                               size_t pstride)
+{
+    __shared__ uint64_t r[LinArgs::MAXT], rs[LinArgs::MAXT];
+    const int row = blockIdx.y, poly = row / nl, i = row - poly * nl;
+    const uint64_t q = pc[i].q;
+    if (threadIdx.x < args.n) {
+        const __int128 v = args.m[threadIdx.x];
+        const u128 av = v < 0 ? (u128)(-v) : (u128)v;
+        uint64_t rr = (uint64_t)(av % q);
+        if (v < 0 && rr) rr = q - rr;
+        r[threadIdx.x] = rr;
+        rs[threadIdx.x] = (uint64_t)(((u128)rr << 64) / q);
+    }
+    __syncthreads();
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const size_t o = (size_t)poly * pstride + (size_t)i * N + c;
+    uint64_t acc = 0;
+    for (int k = 0; k < args.n; k++) acc = add_mod(acc, csub(shoup(args.p[k][o], r[k], rs[k], q), q), q);
+    out[o] = acc;
+}
+
+void k_lincomb(Ctx &c, const LinArgs &args, int level, CtObj &out)
+{
+    ProfScope _ps(c, "lincomb", (uint64_t)2 * (level + 1));
+    k_lincomb_kernel<<<ew_grid(c, 2 * (level + 1)), EW_THREADS, 0, c.stream>>>(args, out.d, c.d_pc, c.N, level + 1,
+                                                                                (size_t)(c.L + 1) * c.N);
+    check_launch("k_lincomb");
 }
 
 // ---------------------------------------------------------------------------

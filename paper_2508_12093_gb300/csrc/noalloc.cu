@@ -115,7 +115,8 @@ extern "C" int ppst_hmult_noalloc(ppst_ctx *ctx, const ppst_evk *evk, const ppst
     if (!k || k->tag != TAG_EVK || !A || A->tag != TAG_CT || !B || B->tag != TAG_CT || !O || O->tag != TAG_CT ||
         A->ctx != c || B->ctx != c || O->ctx != c)
         return c->fail(PPST_E_ARG, "bad handle");
-    if (O == A || O == B) return c->fail(PPST_E_ARG, "the output must not be an input");
+    if (O == A || O == B || O->buf.use_count() != 1)
+        return c->fail(PPST_E_ARG, "the output must own its buffer alone (not an input, not a level view)");
     try {
         hmult_noalloc(*c, *k, *A, *B, *O);
         c->err = Error{0, ""};

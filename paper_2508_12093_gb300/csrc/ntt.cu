@@ -62,6 +62,7 @@ struct PassShape {
     static constexpr int SUB = 16;         // sub-transforms per block
     static constexpr int THREADS = SUB * T;
     static constexpr int SMEM_WORDS = SUB * (M + M / E);  // padded transpose buffer
+    static constexpr int MIN_BLOCKS = THREADS >= 256 ? 3 : 4;  // register cap for occupancy
 };
 
 // Round-1 stages (long distances) on x[k] = word h + T k of a sub-transform.
@@ -72,7 +73,7 @@ struct PassShape {
 
 // one pass of the forward transform
 template <int S, bool COLS>
-__global__ void __launch_bounds__(PassShape<S>::THREADS) k_ntt_fwd_pass(LimbMap map, const PrimeC *__restrict__ pc,
+__global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS) k_ntt_fwd_pass(LimbMap map, const PrimeC *__restrict__ pc,
                                                                         const Tw *__restrict__ tw, int logN)
 {
     typedef PassShape<S> P;
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS) k_ntt_fwd_pass(LimbMap 
 
 // one pass of the inverse transform (mirror image: short distances first)
 template <int S, bool COLS>
-__global__ void __launch_bounds__(PassShape<S>::THREADS) k_ntt_inv_pass(LimbMap map, const PrimeC *__restrict__ pc,
+__global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS) k_ntt_inv_pass(LimbMap map, const PrimeC *__restrict__ pc,
                                                                         const Tw *__restrict__ tw, int logN)
 {
     typedef PassShape<S> P;

@@ -12,7 +12,8 @@
 //    CV (Alg. 6 for a positive mean, no Sign), PCC (Sec. 6.5).
 // Where the paper is silent: the Chebyshev sum is evaluated baby-step
 // giant-step in the Chebyshev basis (T_2i = 2 T_i^2 - 1, T_2i+1 = 2 T_i T_i+1
-// - T_1, giants T_2^m, recursive division by T_n); leaf sums steer every Mul(P)
+// - T_1, giants T_2^m, recursive division by T_n); a leaf sum is one linear
+// combination with integer weights round(c_i q_l) and a single rescale, steered
 // to a common scale so that all Adds see equal scales; Newton's products are
 // associated (x' y)(y y) (depth 2 per step); padding slots of multi-ciphertext
 // columns are corrected with integer multiples of mu^p.
@@ -56,6 +57,12 @@ struct Ev {
     H mul_int(const H &a, int64_t m) { return w(ev_mul_int(c, *a->ct, m)); }
     H mul_const(const H &a, double x, double target = 0) { return w(ev_mul_const(c, *a->ct, x, target)); }
     H hmult(const H &a, const H &b) { return w(ev_hmult(c, k, *a->ct, *b->ct)); }
+    H lin_comb(const std::vector<H> &xs, const std::vector<double> &cs, double target)
+    {
+        std::vector<const CtObj *> p;
+        for (const H &x : xs) p.push_back(x->ct);
+        return w(ev_lin_comb(c, p, cs, target));
+    }
     H drop(const H &a, int l) { return l == a->ct->level ? a : w(ev_drop(c, *a->ct, l)); }
     H rotsum(const H &a) { return w(ev_rotsum(c, k, *a->ct)); }
 };
@@ -123,11 +130,9 @@ struct Cheb {
         if (len <= baby) {
             int lv = 1 << 30;
             for (int i = 1; i < len; i++) lv = std::min(lv, ev.level(T[i]));
-            H acc;
-            for (int i = 1; i < len; i++) {
-                H term = ev.mul_const(ev.drop(T[i], lv), c[i], target);
-                acc = acc ? ev.add(acc, term) : term;
-            }
+            std::vector<H> terms;
+            for (int i = 1; i < len; i++) terms.push_back(ev.drop(T[i], lv));
+            H acc = ev.lin_comb(terms, std::vector<double>(c.begin() + 1, c.end()), target);
             return ev.add_const(acc, c[0]);
         }
         const int n = len / 2;

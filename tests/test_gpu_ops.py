@@ -107,6 +107,20 @@ def test_rescale_and_mul_const(env):
     same(ctx, ctx.mul_const(ctx.drop(ga, 1), 0.9), oc.mul_const(lo, 0.9))
 
 
+def test_lin_comb(env):
+    ctx, sk, evk, oc, ok = env
+    xs, os_, gs = zip(*[fresh(env, 30 + i) for i in range(5)])
+    # different scales: steer one operand first (same op on both sides)
+    o1 = oc.mul_const(os_[1], 1.0, os_[1].scale * (1 + 2.0 ** -28))
+    g1 = ctx.mul_const(gs[1], 1.0, gs[1].scale * (1 + 2.0 ** -28))
+    lv = o1.level
+    olist = [oc.drop(os_[0], lv), o1] + [oc.drop(o, lv) for o in os_[2:]]
+    glist = [ctx.drop(gs[0], lv), g1] + [ctx.drop(g, lv) for g in gs[2:]]
+    coeffs = [0.25, -3.5, 1e-3, 7.0, -0.125]
+    for n in (1, 3, 5):
+        same(ctx, ctx.lin_comb(glist[:n], coeffs[:n], 2.0 ** 40), oc.lin_comb(olist[:n], coeffs[:n], 2.0 ** 40))
+
+
 def test_hmult_all_levels(env):
     ctx, sk, evk, oc, ok = env
     xa, oa, ga = fresh(env, 15)

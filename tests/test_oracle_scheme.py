@@ -95,6 +95,26 @@ def test_homomorphic_ops_match_plaintext(toy):
     assert d.level == 1 and np.abs(dec(d) - x * y).max() < tol
 
 
+def test_lin_comb(toy):
+    c, keys = toy
+    rng = np.random.default_rng(9)
+    xs = [rng.uniform(-1, 1, c.prm.S) for _ in range(3)]
+    cts = [c.encrypt_column(keys["pk"], x, 20 + i)[0] for i, x in enumerate(xs)]
+    cts[1] = c.mul_const(c.drop(cts[1], cts[1].level), 1.0, cts[1].scale * (1 + 2.0 ** -30))
+    lv = min(ct.level for ct in cts)
+    cts = [c.drop(ct, lv) for ct in cts]
+    # one term: exactly Mul(P) with the same target
+    one = c.lin_comb([cts[0]], [0.3], cts[0].scale)
+    ref = c.mul_const(cts[0], 0.3, cts[0].scale)
+    assert np.array_equal(one.c0, ref.c0) and np.array_equal(one.c1, ref.c1) and one.scale == ref.scale
+    # several terms at different scales: the weighted sum, at the target scale
+    coeffs = [0.5, -1.25, 2.0]
+    out = c.lin_comb(cts, coeffs, 2.0 ** 40)
+    assert out.scale == 2.0 ** 40 and out.level == lv - 1
+    want = sum(k * x for k, x in zip(coeffs, xs))
+    assert np.abs(c.decrypt(keys["s"], out) - want).max() < 2.0 ** -20
+
+
 def test_key_switch_changes_key(toy):
     c, keys = toy
     # switching the plain polynomial d (as c1 of (0, d)) under the relin key
