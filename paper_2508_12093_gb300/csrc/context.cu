@@ -260,7 +260,8 @@ void ensure_workspace(Ctx &c)
     c.ws_ext = (uint64_t *)c.pool.get((size_t)c.dnum * c.ext_rows() * N * 8);
     c.ws_acc = (uint64_t *)c.pool.get((size_t)2 * c.ext_rows() * N * 8);
     c.ws_conv = (uint64_t *)c.pool.get((size_t)2 * (c.L + 1) * N * 8);
-    c.ws_bytes = ((size_t)(c.L + 1) + c.dnum * c.ext_rows() + 2 * c.ext_rows() + 2 * (c.L + 1)) * N * 8;
+    c.ws_d2n = (uint64_t *)c.pool.get((size_t)(c.L + 1) * N * 8);
+    c.ws_bytes = ((size_t)2 * (c.L + 1) + c.dnum * c.ext_rows() + 2 * c.ext_rows() + 2 * (c.L + 1)) * N * 8;
 }
 
 // ---------------------------------------------------------------------------
@@ -508,6 +509,50 @@ Ctx *ctx_create(const ppst_params &pin, const ppst_allocator *alloc, cudaStream_
                 c->resc_qmodv[l].c[i] = ql % qi;
             }
         }
+        // fused key switching tables
+        {
+            std::vector<Tw> mo;
+            for (int l = 0; l <= L; l++) {
+                c->modup_outmul_off.push_back(mo.size());
+                for (int i = 0; i <= l; i++) {
+                    const int lo = (i / c->alpha) * c->alpha, hi = std::min(lo + c->alpha, l + 1);
+                    const uint64_t qi = c->primes[i];
+                    uint64_t h = 1;
+                    for (int k = lo; k < hi; k++)
+                        if (k != i) h = h_mulmod(h, c->primes[k] % qi, qi);
+                    const uint64_t v = h_mulmod(c->hpc[i].ninv, h_invmod(h, qi), qi);
+                    mo.push_back(Tw{v, h_shoup(v, qi)});
+                }
+            }
+            c->d_modup_outmul = upload(*c, mo);
+            std::vector<Tw> md(2 * K);
+            for (int b = 0; b < 2 * K; b++) {
+                const int m = b % K;
+                const uint64_t pm = c->primes[L + 1 + m];
+                uint64_t h = 1;
+                for (int k = 0; k < K; k++)
+                    if (k != m) h = h_mulmod(h, c->primes[L + 1 + k] % pm, pm);
+                const uint64_t v = h_mulmod(c->hpc[L + 1 + m].ninv, h_invmod(h, pm), pm);
+                md[b] = Tw{v, h_shoup(v, pm)};
+            }
+            c->d_md_outmul = upload(*c, md);
+            c->md_const.assign((size_t)(L + 1) * (L + 1), MdC{});
+            for (int l = 0; l <= L; l++) {
+                const uint64_t ql = c->primes[l];
+                for (int i = 0; i <= l; i++) {
+                    const uint64_t qi = c->primes[i];
+                    MdC &m = c->md_const[(size_t)l * (L + 1) + i];
+                    const uint64_t pinv = c->pinv.c[i];
+                    const uint64_t qlinv = i < l ? h_invmod(ql % qi, qi) : 0;
+                    const uint64_t pq = h_mulmod(pinv, qlinv, qi);
+                    m.pinv = Tw{pinv, h_shoup(pinv, qi)};
+                    m.qlinv = Tw{qlinv, h_shoup(qlinv, qi)};
+                    m.pq = Tw{pq, h_shoup(pq, qi)};
+                    m.qmod = ql % qi;
+                }
+            }
+            c->d_md_const = upload(*c, c->md_const);
+        }
         PPST_CUDA(cudaStreamSynchronize(stream));
     } catch (...) {
         ctx_destroy(c);
@@ -524,8 +569,9 @@ void ctx_destroy(Ctx *c)
     // (sizes are only needed by user allocators; tables were taken with +256 slack)
     c->pool.trim();
     // device tables and workspace are not in the free lists; release them directly
-    std::vector<void *> own = {c->d_pc, c->d_twf, c->d_twi, c->d_cdt, c->d_ks,
-                               c->ws_d2, c->ws_ext, c->ws_acc, c->ws_conv};
+    std::vector<void *> own = {c->d_pc,          c->d_twf,      c->d_twi,   c->d_cdt,   c->d_ks,
+                               c->d_modup_outmul, c->d_md_outmul, c->d_md_const, c->ws_d2, c->ws_d2n,
+                               c->ws_ext,         c->ws_acc,     c->ws_conv};
     for (void *p : own) {
         if (!p) continue;
         if (c->pool.has_user) c->pool.user.release(c->pool.user.user, p, 0, (void *)c->stream);

@@ -86,9 +86,17 @@ struct ResObj {
     int level_in = 0;
 };
 
-// host-side per-prime data
-struct HostPrime {
-    uint64_t q, psi;
+// offsets of the per-digit base-conversion tables of one level, by value in launches
+struct DigitOffs {
+    uint64_t off[MAXL];
+};
+
+// per (level l, limb i) constants of the fused ModDown + rescale
+struct MdC {
+    Tw pinv;    // P^-1 mod q_i
+    Tw qlinv;   // q_l^-1 mod q_i (i < l)
+    Tw pq;      // P^-1 q_l^-1 mod q_i
+    uint64_t qmod, pad;  // q_l mod q_i
 };
 
 // per-kernel-class timing with CUDA events on the launching stream
@@ -127,11 +135,19 @@ struct Ctx {
     std::vector<ConstVec> resc;                  // [level]: q_l^-1 mod q_i, Shoup (i < l)
     std::vector<ConstVec> resc_qmodv;            // [level]: q_l mod q_i (i < l)
     std::vector<ConstVec> pmod;                  // [0]: P mod q_t for all primes (gadget), Shoup
+    // fused key switching: N^-1 (Q_j/q_i)^-1 per (level, limb); N^-1 (P/p_m)^-1 per P row of both
+    // accumulators; ModDown + rescale constants per (level, limb)
+    Tw *d_modup_outmul = nullptr;
+    std::vector<size_t> modup_outmul_off;
+    Tw *d_md_outmul = nullptr;
+    MdC *d_md_const = nullptr;
+    std::vector<MdC> md_const;
     cudaStream_t stream = nullptr;
     Pool pool;
     Error err{0, ""};
     // workspace (allocated on first key switch)
     uint64_t *ws_d2 = nullptr;   // [L+1][N]
+    uint64_t *ws_d2n = nullptr;  // [L+1][N] key-switch input kept in the evaluation domain
     uint64_t *ws_ext = nullptr;  // [dnum][L+1+K][N]
     uint64_t *ws_acc = nullptr;  // [2][L+1+K][N]
     uint64_t *ws_conv = nullptr; // [2][L+1][N]
@@ -195,6 +211,8 @@ CtObj *ct_view(const CtObj &a, int level);   // a view of limbs 0..level
 // ---- NTT (ntt.cu) ----
 void ntt_fwd(Ctx &c, const LimbMap &m);
 void ntt_inv(Ctx &c, const LimbMap &m);
+// inverse NTT whose final N^-1 is replaced by outmul[b] (N^-1 times a per-limb constant)
+void ntt_inv_mul(Ctx &c, const LimbMap &m, const Tw *outmul);
 LimbMap map_ct(const Ctx &c, uint64_t *d, int level);  // both polys of a ciphertext buffer
 LimbMap map_poly(const Ctx &c, uint64_t *d, int level); // one poly, limbs 0..level
 
@@ -204,6 +222,9 @@ void k_neg(Ctx &c, const CtObj &a, CtObj &out);
 void k_mul_scalar_ct(Ctx &c, const CtObj &a, const ConstVec &cv, CtObj &out);
 void k_add_scalar_c0(Ctx &c, const CtObj &a, const ConstVec &cv, CtObj &out);
 void k_tensor(Ctx &c, const CtObj &a, const CtObj &b, int level, uint64_t *d0, uint64_t *d1, uint64_t *d2);
+// the same, d2 written to two buffers
+void k_tensor2(Ctx &c, const CtObj &a, const CtObj &b, int level, uint64_t *d0, uint64_t *d1, uint64_t *d2,
+               uint64_t *d2b);
 void k_modup(Ctx &c, const uint64_t *d2coef, int level, uint64_t *ext);
 void k_inner_product(Ctx &c, const uint64_t *ext, const Swk &key, int level, uint64_t *acc);
 void k_moddown(Ctx &c, uint64_t *acc, int level, const uint64_t *add0, const uint64_t *add1, uint64_t *out0,

@@ -122,61 +122,7 @@ CtObj *ev_drop(Ctx &c, const CtObj &a, int level)
     return ct_view(a, level);
 }
 
-// hybrid key switch of d (evaluation domain, limbs 0..level, held in ws_d2):
-// out_k = add_k + ModDown(sum_j ModUp_j(d) * key_j,k)
-static void key_switch(Ctx &c, int level, const Swk &key, const uint64_t *add0, const uint64_t *add1, uint64_t *out0,
-                       uint64_t *out1)
-{
-    ensure_workspace(c);
-    ntt_inv(c, map_poly(c, c.ws_d2, level));
-    k_modup(c, c.ws_d2, level, c.ws_ext);
-    LimbMap me{c.ws_ext, c.ext_rows() * c.N, level + 1 + c.K, c.ndigits(level), level + 1, 0, c.L + 1};
-    ntt_fwd(c, me);
-    k_inner_product(c, c.ws_ext, key, level, c.ws_acc);
-    k_moddown(c, c.ws_acc, level, add0, add1, out0, out1);
-}
-
-CtObj *ev_hmult(Ctx &c, const EvkObj &k, const CtObj &a, const CtObj &b)
-{
-    const int lv = std::min(a.level, b.level);
-    if (lv < 1) throw_err(PPST_E_DEPTH, "hmult at level 0");
-    if (!k.relin.d) throw_err(PPST_E_STATE, "no relinearisation key");
-    ensure_workspace(c);
-    CtObj *t = ct_new(c, lv, a.scale * b.scale);
-    CtObj *o = nullptr;
-    try {
-        k_tensor(c, a, b, lv, t->c0(), t->c1(), c.ws_d2);
-        key_switch(c, lv, k.relin, t->c0(), t->c1(), t->c0(), t->c1());
-        o = ct_new(c, lv - 1, (a.scale * b.scale) / (double)c.primes[lv]);
-        k_rescale(c, *t, *o);
-    } catch (...) {
-        ct_free(t);
-        ct_free(o);
-        throw;
-    }
-    ct_free(t);
-    return o;
-}
-
-CtObj *ev_rotate(Ctx &c, const EvkObj &k, const CtObj &a, int r)
-{
-    const int rr = ((r % c.S) + c.S) % c.S;
-    if (rr == 0) return ct_clone(a);
-    auto it = k.rot.find(rr);
-    if (it == k.rot.end()) throw_err(PPST_E_STATE, "no Galois key for rotation " + std::to_string(rr));
-    ensure_workspace(c);
-    const size_t ps = (size_t)(c.L + 1) * c.N;
-    CtObj *o = ct_new(c, a.level, a.scale);
-    try {
-        k_automorph(c, a.d, a.level, galois_elt(c, rr), o->d, ps, 2);
-        k_copy(c, c.ws_d2, o->c1(), (size_t)(a.level + 1) * c.N);
-        key_switch(c, a.level, it->second, o->c0(), nullptr, o->c0(), o->c1());
-    } catch (...) {
-        ct_free(o);
-        throw;
-    }
-    return o;
-}
+// ev_hmult and ev_rotate (fused key switching) are in ks.cu
 
 CtObj *ev_rotsum(Ctx &c, const EvkObj &k, const CtObj &a)
 {

@@ -98,7 +98,7 @@ void k_copy(Ctx &c, uint64_t *dst, const uint64_t *src, size_t words)
 __global__ void __launch_bounds__(EW_THREADS) k_tensor_kernel(const uint64_t *__restrict__ a,
                                                               const uint64_t *__restrict__ b,
                                                               uint64_t *__restrict__ d0, uint64_t *__restrict__ d1,
-                                                              uint64_t *__restrict__ d2,
+                                                              uint64_t *__restrict__ d2, uint64_t *__restrict__ d2b,
                                                               const PrimeC *__restrict__ pc, int N, size_t pstride)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -108,19 +108,27 @@ __global__ void __launch_bounds__(EW_THREADS) k_tensor_kernel(const uint64_t *__
     const size_t off = (size_t)i * N + c;
     const uint64_t x0 = a[off], x1 = a[pstride + off], y0 = b[off], y1 = b[pstride + off];
     d0[off] = mul_mod(x0, y0, p);
-    d2[off] = mul_mod(x1, y1, p);
+    const uint64_t v2 = mul_mod(x1, y1, p);
+    d2[off] = v2;
+    if (d2b) d2b[off] = v2;
     Acc128 acc{0, 0};
     mac(acc, x0, y1);
     mac(acc, x1, y0);
     d1[off] = mont_mul(mont_redc(acc.hi, acc.lo, p.q, p.qinv), p.r2, p.q, p.qinv);
 }
 
-void k_tensor(Ctx &c, const CtObj &a, const CtObj &b, int level, uint64_t *d0, uint64_t *d1, uint64_t *d2)
+void k_tensor2(Ctx &c, const CtObj &a, const CtObj &b, int level, uint64_t *d0, uint64_t *d1, uint64_t *d2,
+               uint64_t *d2b)
 {
-    ProfScope _ps(c, "tensor");
-    k_tensor_kernel<<<ew_grid(c, level + 1), EW_THREADS, 0, c.stream>>>(a.d, b.d, d0, d1, d2, c.d_pc, c.N,
+    ProfScope _ps(c, "tensor", (uint64_t)3 * (level + 1));
+    k_tensor_kernel<<<ew_grid(c, level + 1), EW_THREADS, 0, c.stream>>>(a.d, b.d, d0, d1, d2, d2b, c.d_pc, c.N,
                                                                         (size_t)(c.L + 1) * c.N);
     check_launch("k_tensor");
+}
+
+void k_tensor(Ctx &c, const CtObj &a, const CtObj &b, int level, uint64_t *d0, uint64_t *d1, uint64_t *d2)
+{
+    k_tensor2(c, a, b, level, d0, d1, d2, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -129,9 +137,6 @@ void k_tensor(Ctx &c, const CtObj &a, const CtObj &b, int level, uint64_t *d0, u
 // Digit j covers limbs [j alpha, min((j+1) alpha, level+1)); its own rows are
 // copied, the others are sum_i [d_i (Q_j/q_i)^-1]_{q_i} (Q_j/q_i) mod t.
 // ---------------------------------------------------------------------------
-struct DigitOffs {
-    uint64_t off[MAXL];
-};
 
 __global__ void __launch_bounds__(EW_THREADS) k_modup_kernel(const uint64_t *__restrict__ d2,
                                                              uint64_t *__restrict__ ext,

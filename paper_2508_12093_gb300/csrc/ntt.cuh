@@ -1,0 +1,240 @@
+// ntt.cuh -- device building blocks of the limb NTT (see ntt.cu for the scheme).
+//
+// A pass runs M-point sub-transforms (M = 2^S) of an N-point negacyclic
+// transform: the COLS pass the columns (stride C = N / M), the CHUNKS pass the
+// contiguous chunks of M words. A thread holds E = 2^ceil(S/2) words; the
+// long-distance stages act on words h + T k (T = M / E threads per
+// sub-transform), then one shared-memory transpose, then the short-distance
+// stages act on words E h + k. The cores below take the E words in registers
+// (load layout) and return them in the store layout; kernels supply their own
+// loads and stores, which is how the key-switching kernels fuse base
+// conversion into the load and the key inner product into the store.
+#pragma once
+#include <type_traits>
+
+#include "ctx.cuh"
+
+namespace ppst {
+
+template <int S>
+struct PassShape {
+    static constexpr int M = 1 << S;
+    static constexpr int A = (S + 1) / 2;  // register stages of round 1
+    static constexpr int E = 1 << A;       // words per thread
+    static constexpr int T = M / E;        // threads per sub-transform
+    static constexpr int SUB = 16;         // sub-transforms per block
+    static constexpr int THREADS = SUB * T;
+    static constexpr int SMEM_WORDS = SUB * (M + M / E);  // padded transpose buffer
+    static constexpr int MIN_BLOCKS = THREADS >= 256 ? 3 : 4;
+};
+
+// forward lazy butterfly: X, Y in [0, 4q) -> [0, 4q)
+__device__ __forceinline__ void bfly_fwd(uint64_t &X, uint64_t &Y, const Tw &w, uint64_t q, uint64_t q2)
+{
+    uint64_t x = X >= q2 ? X - q2 : X;
+    uint64_t t = shoup(Y, w.w, w.s, q);
+    X = x + t;
+    Y = x - t + q2;
+}
+
+// inverse lazy butterfly: X, Y in [0, 2q) -> [0, 2q)
+__device__ __forceinline__ void bfly_inv(uint64_t &X, uint64_t &Y, const Tw &w, uint64_t q, uint64_t q2)
+{
+    uint64_t s = X + Y;
+    uint64_t d = X - Y + q2;
+    X = s >= q2 ? s - q2 : s;
+    Y = shoup(d, w.w, w.s, q);
+}
+
+__device__ __forceinline__ uint64_t reduce4q(uint64_t x, uint64_t q)
+{
+    uint64_t q2 = 2 * q;
+    x = x >= q2 ? x - q2 : x;
+    return x >= q ? x - q : x;
+}
+
+__device__ __forceinline__ Tw ldtw(const Tw *p)
+{
+    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+    return Tw{v.x, v.y};
+}
+
+// thread coordinates of a pass: COLS -> (sub = column in block, h), CHUNKS -> (h, sub = chunk in block)
+template <int S, bool COLS>
+__device__ __forceinline__ void pass_coords(int &h, int &sub)
+{
+    typedef PassShape<S> P;
+    if (COLS) {
+        sub = threadIdx.x % P::SUB;
+        h = threadIdx.x / P::SUB;
+    } else {
+        h = threadIdx.x % P::T;
+        sub = threadIdx.x / P::T;
+    }
+}
+
+// ---- forward, COLS pass: stages with m = 1 .. M/2 (distances in rows) ----
+template <int S>
+__device__ __forceinline__ void cols_fwd_core(uint64_t (&x)[PassShape<S>::E], uint64_t *sm, int h, int sub,
+                                              const Tw *__restrict__ T, uint64_t q)
+{
+    typedef PassShape<S> P;
+    const uint64_t q2 = 2 * q;
+#pragma unroll
+    for (int s = P::A - 1; s >= 0; s--) {
+        const int d = P::T << s;
+        const int mg = P::M / (2 * d);
+#pragma unroll
+        for (int k = 0; k < P::E; k++) {
+            if ((k >> s) & 1) continue;
+            bfly_fwd(x[k], x[k + (1 << s)], ldtw(T + mg + (k >> (s + 1))), q, q2);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < P::E; k++) sm[(h + P::T * k) * P::SUB + sub] = x[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < P::E; k++) x[k] = sm[(P::E * h + k) * P::SUB + sub];
+#pragma unroll
+    for (int d = P::T / 2; d >= 1; d >>= 1) {
+        const int mg = P::M / (2 * d);
+#pragma unroll
+        for (int k = 0; k < P::E; k++) {
+            if (k & d) continue;
+            bfly_fwd(x[k], x[k + d], ldtw(T + mg + (P::E * h + k) / (2 * d)), q, q2);
+        }
+    }
+}
+
+// ---- forward, CHUNKS pass: stages with m = N/M .. N/2 on chunk g ----
+template <int S>
+__device__ __forceinline__ void chunks_fwd_core(uint64_t (&x)[PassShape<S>::E], uint64_t *sm, int h, int sub, int g,
+                                                int N, const Tw *__restrict__ T, uint64_t q)
+{
+    typedef PassShape<S> P;
+    const uint64_t q2 = 2 * q;
+#pragma unroll
+    for (int s = P::A - 1; s >= 0; s--) {
+        const int d = P::T << s;
+        const int mg = N / (2 * d);
+        const int ib = g * (P::M / (2 * d));
+#pragma unroll
+        for (int k = 0; k < P::E; k++) {
+            if ((k >> s) & 1) continue;
+            bfly_fwd(x[k], x[k + (1 << s)], ldtw(T + mg + ib + (k >> (s + 1))), q, q2);
+        }
+    }
+    uint64_t *ssub = sm + sub * (P::M + P::M / P::E);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < P::E; k++) {
+        const int e = h + P::T * k;
+        ssub[e + e / P::E] = x[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < P::E; k++) x[k] = ssub[(P::E + 1) * h + k];
+#pragma unroll
+    for (int d = P::T / 2; d >= 1; d >>= 1) {
+        const int mg = N / (2 * d);
+        const int ib = g * (P::M / (2 * d));
+#pragma unroll
+        for (int k = 0; k < P::E; k++) {
+            if (k & d) continue;
+            bfly_fwd(x[k], x[k + d], ldtw(T + mg + ib + (P::E * h + k) / (2 * d)), q, q2);
+        }
+    }
+}
+
+// ---- inverse, CHUNKS pass (first inverse pass): words E h + k in, h + T k out ----
+template <int S>
+__device__ __forceinline__ void chunks_inv_core(uint64_t (&x)[PassShape<S>::E], uint64_t *sm, int h, int sub, int g,
+                                                int N, const Tw *__restrict__ T, uint64_t q)
+{
+    typedef PassShape<S> P;
+    const uint64_t q2 = 2 * q;
+#pragma unroll
+    for (int d = 1; d <= P::T / 2; d <<= 1) {
+        const int mg = N / (2 * d);
+        const int ib = g * (P::M / (2 * d));
+#pragma unroll
+        for (int k = 0; k < P::E; k++) {
+            if (k & d) continue;
+            bfly_inv(x[k], x[k + d], ldtw(T + mg + ib + (P::E * h + k) / (2 * d)), q, q2);
+        }
+    }
+    uint64_t *ssub = sm + sub * (P::M + P::M / P::E);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < P::E; k++) ssub[(P::E + 1) * h + k] = x[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < P::E; k++) {
+        const int e = h + P::T * k;
+        x[k] = ssub[e + e / P::E];
+    }
+#pragma unroll
+    for (int s = 0; s < P::A; s++) {
+        const int d = P::T << s;
+        const int mg = N / (2 * d);
+        const int ib = g * (P::M / (2 * d));
+#pragma unroll
+        for (int k = 0; k < P::E; k++) {
+            if ((k >> s) & 1) continue;
+            bfly_inv(x[k], x[k + (1 << s)], ldtw(T + mg + ib + (k >> (s + 1))), q, q2);
+        }
+    }
+}
+
+// ---- inverse, COLS pass (last inverse pass): rows E h + k in, h + T k out ----
+template <int S>
+__device__ __forceinline__ void cols_inv_core(uint64_t (&x)[PassShape<S>::E], uint64_t *sm, int h, int sub,
+                                              const Tw *__restrict__ T, uint64_t q)
+{
+    typedef PassShape<S> P;
+    const uint64_t q2 = 2 * q;
+#pragma unroll
+    for (int d = 1; d <= P::T / 2; d <<= 1) {
+        const int mg = P::M / (2 * d);
+#pragma unroll
+        for (int k = 0; k < P::E; k++) {
+            if (k & d) continue;
+            bfly_inv(x[k], x[k + d], ldtw(T + mg + (P::E * h + k) / (2 * d)), q, q2);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < P::E; k++) sm[(P::E * h + k) * P::SUB + sub] = x[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < P::E; k++) x[k] = sm[(h + P::T * k) * P::SUB + sub];
+#pragma unroll
+    for (int s = 0; s < P::A; s++) {
+        const int d = P::T << s;
+        const int mg = P::M / (2 * d);
+#pragma unroll
+        for (int k = 0; k < P::E; k++) {
+            if ((k >> s) & 1) continue;
+            bfly_inv(x[k], x[k + (1 << s)], ldtw(T + mg + (k >> (s + 1))), q, q2);
+        }
+    }
+}
+
+// calls f(std::integral_constant<int, s>) for the pass sizes of N = 2^10 .. 2^16
+template <class F>
+void dispatch_s(int s, F &&f)
+{
+    switch (s) {
+    case 5: f(std::integral_constant<int, 5>{}); break;
+    case 6: f(std::integral_constant<int, 6>{}); break;
+    case 7: f(std::integral_constant<int, 7>{}); break;
+    case 8: f(std::integral_constant<int, 8>{}); break;
+    default: throw_err(PPST_E_ARG, "unsupported ring degree for the NTT");
+    }
+}
+
+inline int ntt_s_rows(int logN) { return (logN + 1) / 2; }  // COLS pass: log2 R
+inline int ntt_s_chunk(int logN) { return logN / 2; }      // CHUNKS pass: log2 C
+
+}  // namespace ppst

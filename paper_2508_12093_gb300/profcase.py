@@ -1,0 +1,43 @@
+"""Small, self-contained GPU workloads for profiler captures (ncu).
+
+    python -m paper_2508_12093_gb300.profcase hmult      # N=2^16, 3 top-level HMult+KS
+    python -m paper_2508_12093_gb300.profcase rotate     # N=2^16, 3 top-level rotations
+    python -m paper_2508_12093_gb300.profcase query      # N=2^16, one kurtosis query
+
+Each case sets up keys and one ciphertext, runs a few warm-up iterations, then
+the profiled iterations, synchronises and prints "ok".
+"""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(case):
+    import paper_2508_12093_gb300 as pp
+    import workloads
+    ctx = pp.Context(workloads.PARAMS["n16_d6"])
+    if case in ("hmult", "rotate"):
+        sk, evk = ctx.keygen(2, rotations=[1])
+        a = ctx.encrypt_ints(evk, np.zeros(ctx.N, dtype=np.int64), 9, 0, 2.0 ** 50)
+        op = (lambda: ctx.hmult(evk, a, a)) if case == "hmult" else (lambda: ctx.rotate(evk, a, 1))
+        for _ in range(2):
+            op()
+        for _ in range(3):
+            op()
+    elif case == "query":
+        sk, evk = ctx.keygen(2)
+        col = ctx.encrypt_column(evk, workloads.lognormal_column(ctx.S, seed=1), 3)
+        ctx.query(evk, "kurt", col, opts=dict(B_x=20.0, cheb_log2deg=7, newton_steps=3))
+    else:
+        raise SystemExit(f"unknown case {case}")
+    ctx.sync()
+    print("ok")
+
+
+if __name__ == "__main__":
+    main(sys.argv[1] if len(sys.argv) > 1 else "hmult")
