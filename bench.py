@@ -308,10 +308,10 @@ def main():
     value = queries / (t_ms / 1000.0)
     lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
 
-    # roofline of the dominant kernel: algorithmic bytes = one read and one
-    # write of every limb it processes (transform passes, elementwise kernels)
+    # roofline of the dominant kernel: algorithmic bytes = the limbs it must
+    # read once plus the limbs it writes (the library counts them per launch)
     peak, peak_kind = peaks()
-    alg_bytes = units_dom * 2 * 8 * ctx.N
+    alg_bytes = units_dom * 8 * ctx.N
     achieved = (alg_bytes / (ms_dom / 1000.0)) / 1e9 if ms_dom > 0 else None
 
     # HMult + key switch microbenchmark (top level, dnum = 6)

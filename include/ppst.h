@@ -253,13 +253,16 @@ int ppst_ticket_latency(ppst_server *srv, uint64_t ticket, double *seconds);
 /* ---- kernel timing ----------------------------------------------------------
  * While profiling is on, every launch of the named kernel class (NULL or "":
  * every class) is bracketed by CUDA events on the context's stream. Classes:
- * ntt_cols_fwd, ntt_chunks_fwd, ntt_chunks_inv, ntt_cols_inv, modup,
- * inner_product, moddown_conv, moddown_final, rescale_bcast, rescale_final,
- * tensor, automorph, elementwise, copy. ppst_prof_read synchronises, returns
- * the launch count, summed device time and summed work units (limbs of N words
- * for the transforms) of one class, and forgets them. ppst_prof_classes writes
- * the recorded class names, comma separated. ppst_launch_count: kernels this
- * context has launched so far (always counted, profiling on or off). */
+ * ntt_cols_fwd, ntt_chunks_fwd, ntt_chunks_inv, ntt_cols_inv (transform
+ * passes), modup_cols, inner_chunks, moddown_top, moddown_cols, moddown_chunks
+ * (fused key switching), modup, inner_product, moddown_conv, moddown_final
+ * (unfused key switching), rescale_bcast, rescale_final, tensor, automorph,
+ * lincomb, elementwise, copy. ppst_prof_read synchronises, returns the launch
+ * count, summed device time and summed algorithmic traffic of one class, and
+ * forgets them; the traffic is counted in limbs of N words (8N bytes each), as
+ * the limbs a kernel must read once plus the limbs it writes. ppst_prof_classes
+ * writes the recorded class names, comma separated. ppst_launch_count: kernels
+ * this context has launched so far (always counted, profiling on or off). */
 int ppst_prof_start(ppst_ctx *ctx, const char *kernel_class);
 int ppst_prof_stop(ppst_ctx *ctx);
 int ppst_prof_read(ppst_ctx *ctx, const char *kernel_class, uint64_t *launches, double *total_ms,

@@ -37,8 +37,8 @@ __global__ void __launch_bounds__(EW_THREADS) k_ct_ew(const uint64_t *__restrict
 
 void k_add(Ctx &c, const CtObj &a, const CtObj &b, CtObj &out, bool sub)
 {
-    ProfScope _ps(c, "elementwise");
     const int nl = out.level + 1;
+    ProfScope _ps(c, "elementwise", (uint64_t)6 * nl);  // limbs moved: 2 x 2nl read, 2nl written
     ConstVec cv{};
     if (sub)
         k_ct_ew<EW_SUB><<<ew_grid(c, 2 * nl), EW_THREADS, 0, c.stream>>>(a.d, b.d, out.d, c.d_pc, cv, c.N, nl,
@@ -51,8 +51,8 @@ void k_add(Ctx &c, const CtObj &a, const CtObj &b, CtObj &out, bool sub)
 
 void k_neg(Ctx &c, const CtObj &a, CtObj &out)
 {
-    ProfScope _ps(c, "elementwise");
     const int nl = out.level + 1;
+    ProfScope _ps(c, "elementwise", (uint64_t)4 * nl);
     ConstVec cv{};
     k_ct_ew<EW_NEG><<<ew_grid(c, 2 * nl), EW_THREADS, 0, c.stream>>>(a.d, nullptr, out.d, c.d_pc, cv, c.N, nl,
                                                                      (size_t)(c.L + 1) * c.N);
@@ -61,8 +61,8 @@ void k_neg(Ctx &c, const CtObj &a, CtObj &out)
 
 void k_mul_scalar_ct(Ctx &c, const CtObj &a, const ConstVec &cv, CtObj &out)
 {
-    ProfScope _ps(c, "elementwise");
     const int nl = out.level + 1;
+    ProfScope _ps(c, "elementwise", (uint64_t)4 * nl);
     k_ct_ew<EW_MULC><<<ew_grid(c, 2 * nl), EW_THREADS, 0, c.stream>>>(a.d, nullptr, out.d, c.d_pc, cv, c.N, nl,
                                                                       (size_t)(c.L + 1) * c.N);
     check_launch("k_ct_ew mulc");
@@ -70,8 +70,8 @@ void k_mul_scalar_ct(Ctx &c, const CtObj &a, const ConstVec &cv, CtObj &out)
 
 void k_add_scalar_c0(Ctx &c, const CtObj &a, const ConstVec &cv, CtObj &out)
 {
-    ProfScope _ps(c, "elementwise");
     const int nl = out.level + 1;
+    ProfScope _ps(c, "elementwise", (uint64_t)4 * nl);
     k_ct_ew<EW_ADDC0><<<ew_grid(c, 2 * nl), EW_THREADS, 0, c.stream>>>(a.d, nullptr, out.d, c.d_pc, cv, c.N, nl,
                                                                        (size_t)(c.L + 1) * c.N);
     check_launch("k_ct_ew addc0");
@@ -86,7 +86,7 @@ __global__ void k_copy_kernel(uint64_t *__restrict__ dst, const uint64_t *__rest
 void k_copy(Ctx &c, uint64_t *dst, const uint64_t *src, size_t words)
 {
     if (!words) return;
-    ProfScope _ps(c, "copy", words / c.N);
+    ProfScope _ps(c, "copy", 2 * words / c.N);
     const size_t blocks = std::min<size_t>((words + 255) / 256, 4096);
     k_copy_kernel<<<(unsigned)blocks, 256, 0, c.stream>>>(dst, src, words);
     check_launch("k_copy");
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(EW_THREADS) k_tensor_kernel(const uint64_t *__
 void k_tensor2(Ctx &c, const CtObj &a, const CtObj &b, int level, uint64_t *d0, uint64_t *d1, uint64_t *d2,
                uint64_t *d2b)
 {
-    ProfScope _ps(c, "tensor", (uint64_t)3 * (level + 1));
+    ProfScope _ps(c, "tensor", (uint64_t)(d2b ? 8 : 7) * (level + 1));
     k_tensor_kernel<<<ew_grid(c, level + 1), EW_THREADS, 0, c.stream>>>(a.d, b.d, d0, d1, d2, d2b, c.d_pc, c.N,
                                                                         (size_t)(c.L + 1) * c.N);
     check_launch("k_tensor");
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(EW_THREADS) k_modup_kernel(const uint64_t *__r
 
 void k_modup(Ctx &c, const uint64_t *d2coef, int level, uint64_t *ext)
 {
-    ProfScope _ps(c, "modup");
+    ProfScope _ps(c, "modup", (uint64_t)(level + 1) + (uint64_t)c.ndigits(level) * (level + 1 + c.K));
     const int nd = c.ndigits(level);
     DigitOffs offs;
     for (int j = 0; j < nd; j++) offs.off[j] = c.modup_off[level][j];
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(EW_THREADS) k_inner_kernel(const uint64_t *__r
 
 void k_inner_product(Ctx &c, const uint64_t *ext, const Swk &key, int level, uint64_t *acc)
 {
-    ProfScope _ps(c, "inner_product");
+    ProfScope _ps(c, "inner_product", (uint64_t)(level + 1 + c.K) * (3 * c.ndigits(level) + 2));
     const int E = level + 1 + c.K;
     k_inner_kernel<<<ew_grid(c, E), EW_THREADS, 0, c.stream>>>(ext, key.d, acc, c.d_pc, c.N, level, c.L, c.K,
                                                                c.ndigits(level), c.ext_rows() * c.N);
@@ -283,14 +283,14 @@ void k_moddown(Ctx &c, uint64_t *acc, int level, const uint64_t *add0, const uin
     LimbMap mp{acc + (size_t)(level + 1) * c.N, es, c.K, 2, 0, 0, c.L + 1};
     ntt_inv(c, mp);
     {
-        ProfScope _ps(c, "moddown_conv");
+        ProfScope _ps(c, "moddown_conv", (uint64_t)2 * c.K + 2 * (level + 1));
         k_moddown_conv_kernel<<<ew_grid(c, 2), EW_THREADS, 0, c.stream>>>(acc, c.ws_conv, c.d_ks + c.moddown_off,
                                                                           c.d_pc, c.N, level, c.L, c.K, es, cs);
         check_launch("k_moddown_conv");
     }
     LimbMap mq{c.ws_conv, cs, level + 1, 2, level + 1, 0, 0};
     ntt_fwd(c, mq);
-    ProfScope _ps(c, "moddown_final");
+    ProfScope _ps(c, "moddown_final", (uint64_t)8 * (level + 1));
     k_moddown_final_kernel<<<ew_grid(c, 2 * (level + 1)), EW_THREADS, 0, c.stream>>>(
         acc, c.ws_conv, add0, add1, out0, out1, c.d_pc, c.pinv, c.N, level + 1, es, cs);
     check_launch("k_moddown_final");
@@ -352,7 +352,7 @@ void k_rescale_mul(Ctx &c, const CtObj &a, const ConstVec *mul, CtObj &out)
     // top limb of c0 and c1 (times m_l) -> scratch rows [0], [1] of ws_d2, to the coefficient domain
     uint64_t *top = c.ws_d2;
     {
-        ProfScope _ps(c, "copy", 2);
+        ProfScope _ps(c, "copy", 4);
         const uint64_t m = mul ? mul->c[l] : 1, msh = mul ? mul->sh[l] : h_shoup(1, ql);
         k_top_copy_kernel<<<ew_grid(c, 2), EW_THREADS, 0, c.stream>>>(a.d, top, ql, m, msh, c.N,
                                                                         (size_t)l * c.N, ps + (size_t)l * c.N);
@@ -361,7 +361,7 @@ void k_rescale_mul(Ctx &c, const CtObj &a, const ConstVec *mul, CtObj &out)
     LimbMap mt{top, (size_t)c.N, 1, 2, 1, l, 0};
     ntt_inv(c, mt);
     {
-        ProfScope _ps(c, "rescale_bcast");
+        ProfScope _ps(c, "rescale_bcast", (uint64_t)2 + 2 * l);
         k_rescale_bcast_kernel<<<ew_grid(c, 2 * l), EW_THREADS, 0, c.stream>>>(top, c.ws_conv, c.d_pc,
                                                                                 c.resc_qmodv[l], c.N, l, ps);
         check_launch("k_rescale_bcast");
@@ -374,7 +374,7 @@ void k_rescale_mul(Ctx &c, const CtObj &a, const ConstVec *mul, CtObj &out)
         mq.c[i] = mul ? h_mulmod(mul->c[i], c.resc[l].c[i], qi) : c.resc[l].c[i];
         mq.sh[i] = h_shoup(mq.c[i], qi);
     }
-    ProfScope _ps(c, "rescale_final", 2 * l);
+    ProfScope _ps(c, "rescale_final", (uint64_t)6 * l);
     k_rescale_final_kernel<<<ew_grid(c, 2 * l), EW_THREADS, 0, c.stream>>>(a.d, c.ws_conv, out.d, c.d_pc, c.resc[l],
                                                                             mq, c.N, l, ps);
     check_launch("k_rescale_final");
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(EW_THREADS) k_lincomb_kernel(LinArgs args, uin
 
 void k_lincomb(Ctx &c, const LinArgs &args, int level, CtObj &out)
 {
-    ProfScope _ps(c, "lincomb", (uint64_t)2 * (level + 1));
+    ProfScope _ps(c, "lincomb", (uint64_t)(args.n + 1) * 2 * (level + 1));
     k_lincomb_kernel<<<ew_grid(c, 2 * (level + 1)), EW_THREADS, 0, c.stream>>>(args, out.d, c.d_pc, c.N, level + 1,
                                                                                 (size_t)(c.L + 1) * c.N);
     check_launch("k_lincomb");
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(EW_THREADS) k_automorph_kernel(const uint64_t 
 
 void k_automorph(Ctx &c, const uint64_t *in, int level, uint64_t galois, uint64_t *out, size_t poly_stride, int npoly)
 {
-    ProfScope _ps(c, "automorph");
+    ProfScope _ps(c, "automorph", (uint64_t)2 * npoly * (level + 1));
     k_automorph_kernel<<<ew_grid(c, npoly * (level + 1)), EW_THREADS, 0, c.stream>>>(in, out, c.logN, level + 1,
                                                                                       galois, poly_stride);
     check_launch("k_automorph");

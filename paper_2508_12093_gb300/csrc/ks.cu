@@ -306,7 +306,9 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key)
     for (int j = 0; j < nd; j++) offs.off[j] = c.modup_off[level][j];
     const size_t es = c.ext_rows() * c.N;
     {
-        ProfScope _ps(c, "modup_cols", (uint64_t)nd * E_ext);
+        uint64_t targets = 0;
+        for (int j = 0; j < nd; j++) targets += E_ext - (std::min((j + 1) * c.alpha, level + 1) - j * c.alpha);
+        ProfScope _ps(c, "modup_cols", (uint64_t)(level + 1) + targets);  // limbs moved: d read once, targets written
         dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
             constexpr int S = decltype(sv)::value;
             dispatch_a(c.alpha, [&](auto av) {
@@ -317,7 +319,8 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key)
         });
         check_launch("k_modup_cols");
     }
-    ProfScope _ps(c, "inner_chunks", (uint64_t)nd * E_ext);
+    // per target limb: one digit word and two key words per digit read, two accumulators written
+    ProfScope _ps(c, "inner_chunks", (uint64_t)E_ext * (3 * nd + 2));
     dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
         k_inner_chunks<S><<<grid_s(c, S, E_ext), PassShape<S>::THREADS, 0, c.stream>>>(
@@ -337,7 +340,7 @@ static void ks_moddown(Ctx &c, int level, const uint64_t *d, const uint64_t *add
     const MdC &hm = c.md_const[(size_t)level * (c.L + 1) + level];
     uint64_t *top = c.ws_d2;  // [2][N], free once ModUp has run
     if (RESC) {
-        ProfScope _ps(c, "moddown_top", 2);
+        ProfScope _ps(c, "moddown_top", 6);
         k_md_top_kernel<<<dim3(c.N / 256, 2), 256, 0, c.stream>>>(d, c.ws_acc, top, c.d_pc, hm.pinv, c.N, level, ps,
                                                                    es);
         check_launch("k_md_top");
@@ -349,13 +352,13 @@ static void ks_moddown(Ctx &c, int level, const uint64_t *d, const uint64_t *add
     if (RESC) {
         LimbMap mt{top, (size_t)c.N, 1, 2, 1, level, 0};
         ntt_inv(c, mt);
-        ProfScope _ps(c, "moddown_top", 2);
+        ProfScope _ps(c, "moddown_top", (uint64_t)2 * c.K + 4);
         k_md_topfix_kernel<<<dim3(c.N / 256, 2), 256, 0, c.stream>>>(c.ws_acc, top, hMP, c.d_pc, hm.pinv, c.N, level,
                                                                       c.L, c.K, es);
         check_launch("k_md_topfix");
     }
     {
-        ProfScope _ps(c, "moddown_cols", (uint64_t)2 * nl);
+        ProfScope _ps(c, "moddown_cols", (uint64_t)2 * c.K + (RESC ? 2 : 0) + 2 * nl);
         dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
             constexpr int S = decltype(sv)::value;
             dispatch_a(c.K, [&](auto kv) {
@@ -366,7 +369,7 @@ static void ks_moddown(Ctx &c, int level, const uint64_t *d, const uint64_t *add
         });
         check_launch("k_md_cols");
     }
-    ProfScope _ps(c, "moddown_chunks", (uint64_t)2 * nl);
+    ProfScope _ps(c, "moddown_chunks", (uint64_t)(RESC ? 8 : 7) * nl);
     dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
         const uint64_t *a0 = RESC ? d : add0;

@@ -123,14 +123,14 @@ void ntt_fwd(Ctx &c, const LimbMap &m)
 {
     if (m.count() == 0) return;
     {
-        ProfScope _ps(c, "ntt_cols_fwd", (uint64_t)m.count());
+        ProfScope _ps(c, "ntt_cols_fwd", (uint64_t)2 * m.count());
         dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
             constexpr int S = decltype(sv)::value;
             k_ntt_fwd_cols<S><<<pass_grid<S>(c, m), PassShape<S>::THREADS, 0, c.stream>>>(m, c.d_pc, c.d_twf, c.logN);
         });
         check_launch("ntt_cols_fwd");
     }
-    ProfScope _ps(c, "ntt_chunks_fwd", (uint64_t)m.count());
+    ProfScope _ps(c, "ntt_chunks_fwd", (uint64_t)2 * m.count());
     dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
         k_ntt_fwd_chunks<S><<<pass_grid<S>(c, m), PassShape<S>::THREADS, 0, c.stream>>>(m, c.d_pc, c.d_twf, c.logN);
@@ -142,7 +142,7 @@ void ntt_inv_mul(Ctx &c, const LimbMap &m, const Tw *outmul)
 {
     if (m.count() == 0) return;
     {
-        ProfScope _ps(c, "ntt_chunks_inv", (uint64_t)m.count());
+        ProfScope _ps(c, "ntt_chunks_inv", (uint64_t)2 * m.count());
         dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
             constexpr int S = decltype(sv)::value;
             k_ntt_inv_chunks<S><<<pass_grid<S>(c, m), PassShape<S>::THREADS, 0, c.stream>>>(m, c.d_pc, c.d_twi,
@@ -150,7 +150,7 @@ void ntt_inv_mul(Ctx &c, const LimbMap &m, const Tw *outmul)
         });
         check_launch("ntt_chunks_inv");
     }
-    ProfScope _ps(c, "ntt_cols_inv", (uint64_t)m.count());
+    ProfScope _ps(c, "ntt_cols_inv", (uint64_t)2 * m.count());
     dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
         k_ntt_inv_cols<S><<<pass_grid<S>(c, m), PassShape<S>::THREADS, 0, c.stream>>>(m, c.d_pc, c.d_twi, c.logN,
