@@ -156,6 +156,7 @@ uint64_t h_mod_i128(__int128 v, uint64_t q)
 // ---------------------------------------------------------------------------
 void *Pool::get(size_t bytes)
 {
+    std::lock_guard<std::recursive_mutex> lk(mu);
     auto &v = free_[bytes];
     if (!v.empty()) {
         void *p = v.back();
@@ -184,6 +185,7 @@ void *Pool::get(size_t bytes)
 void Pool::put(void *p, size_t bytes)
 {
     if (!p) return;
+    std::lock_guard<std::recursive_mutex> lk(mu);
     free_[bytes].push_back(p);
     in_use -= bytes;
     cached += bytes;
@@ -191,6 +193,7 @@ void Pool::put(void *p, size_t bytes)
 
 void Pool::trim()
 {
+    std::lock_guard<std::recursive_mutex> lk(mu);
     cudaStreamSynchronize(stream);
     for (auto &kv : free_) {
         for (void *p : kv.second) {
@@ -252,16 +255,29 @@ LimbMap map_poly(const Ctx &c, uint64_t *d, int level)
     return LimbMap{d, (size_t)(c.L + 1) * c.N, level + 1, 1, level + 1, 0, 0};
 }
 
-void ensure_workspace(Ctx &c)
+void ensure_workspace(Ctx &c, int items)
 {
-    if (c.ws_d2) return;
-    const size_t N = c.N;
-    c.ws_d2 = (uint64_t *)c.pool.get((size_t)(c.L + 1) * N * 8);
-    c.ws_ext = (uint64_t *)c.pool.get((size_t)c.dnum * c.ext_rows() * N * 8);
-    c.ws_acc = (uint64_t *)c.pool.get((size_t)2 * c.ext_rows() * N * 8);
-    c.ws_conv = (uint64_t *)c.pool.get((size_t)2 * (c.L + 1) * N * 8);
-    c.ws_d2n = (uint64_t *)c.pool.get((size_t)(c.L + 1) * N * 8);
-    c.ws_bytes = ((size_t)2 * (c.L + 1) + c.dnum * c.ext_rows() + 2 * c.ext_rows() + 2 * (c.L + 1)) * N * 8;
+    if (c.ws_items >= items && c.ws_d2) return;
+    const size_t N = c.N, B = (size_t)std::max(items, c.ws_items);
+    const size_t q = c.L + 1, e = c.ext_rows();
+    if (c.ws_d2) {  // grow: the old buffers go back to the pool once the stream is past them
+        c.pool.put(c.ws_d2, (size_t)c.ws_items * q * N * 8);
+        c.pool.put(c.ws_d2n, (size_t)c.ws_items * q * N * 8);
+        c.pool.put(c.ws_ext, (size_t)c.ws_items * c.dnum * e * N * 8);
+        c.pool.put(c.ws_acc, (size_t)c.ws_items * 2 * e * N * 8);
+        c.pool.put(c.ws_conv, (size_t)c.ws_items * 2 * q * N * 8);
+        c.pool.put(c.ws_top, (size_t)c.ws_items * 2 * N * 8);
+        c.ws_d2 = c.ws_d2n = c.ws_ext = c.ws_acc = c.ws_conv = c.ws_top = nullptr;
+        c.ws_items = 0;
+    }
+    c.ws_d2 = (uint64_t *)c.pool.get(B * q * N * 8);
+    c.ws_d2n = (uint64_t *)c.pool.get(B * q * N * 8);
+    c.ws_ext = (uint64_t *)c.pool.get(B * c.dnum * e * N * 8);
+    c.ws_acc = (uint64_t *)c.pool.get(B * 2 * e * N * 8);
+    c.ws_conv = (uint64_t *)c.pool.get(B * 2 * q * N * 8);
+    c.ws_top = (uint64_t *)c.pool.get(B * 2 * N * 8);
+    c.ws_items = (int)B;
+    c.ws_bytes = B * (2 * q + c.dnum * e + 2 * e + 2 * q + 2) * N * 8;
 }
 
 // ---------------------------------------------------------------------------
@@ -571,7 +587,7 @@ void ctx_destroy(Ctx *c)
     // device tables and workspace are not in the free lists; release them directly
     std::vector<void *> own = {c->d_pc,          c->d_twf,      c->d_twi,   c->d_cdt,   c->d_ks,
                                c->d_modup_outmul, c->d_md_outmul, c->d_md_const, c->ws_d2, c->ws_d2n,
-                               c->ws_ext,         c->ws_acc,     c->ws_conv};
+                               c->ws_ext,         c->ws_acc,     c->ws_conv, c->ws_top};
     for (void *p : own) {
         if (!p) continue;
         if (c->pool.has_user) c->pool.user.release(c->pool.user.user, p, 0, (void *)c->stream);

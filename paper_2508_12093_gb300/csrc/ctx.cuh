@@ -31,6 +31,7 @@ struct Pool {
     cudaStream_t stream = nullptr;
     std::unordered_map<size_t, std::vector<void *>> free_;
     size_t in_use = 0, cached = 0;
+    std::recursive_mutex mu;  // batched queries release ciphertexts from their own threads
     void *get(size_t bytes);
     void put(void *p, size_t bytes);
     void trim();
@@ -146,11 +147,14 @@ struct Ctx {
     Pool pool;
     Error err{0, ""};
     // workspace (allocated on first key switch)
+    // (each with a leading item dimension of ws_items for batched key switching)
     uint64_t *ws_d2 = nullptr;   // [L+1][N]
     uint64_t *ws_d2n = nullptr;  // [L+1][N] key-switch input kept in the evaluation domain
     uint64_t *ws_ext = nullptr;  // [dnum][L+1+K][N]
     uint64_t *ws_acc = nullptr;  // [2][L+1+K][N]
     uint64_t *ws_conv = nullptr; // [2][L+1][N]
+    uint64_t *ws_top = nullptr;  // [2][N]
+    int ws_items = 0;
     size_t ws_bytes = 0;
 
     size_t ct_words() const { return (size_t)2 * (L + 1) * N; }
@@ -202,7 +206,7 @@ uint64_t h_mod_i128(__int128 v, uint64_t q);
 // ---- context (context.cu) ----
 Ctx *ctx_create(const ppst_params &p, const ppst_allocator *alloc, cudaStream_t stream);
 void ctx_destroy(Ctx *c);
-void ensure_workspace(Ctx &c);
+void ensure_workspace(Ctx &c, int items = 1);  // key-switch workspace for `items` ciphertexts
 CtObj *ct_new(Ctx &c, int level, double scale);
 void ct_free(CtObj *ct);
 CtObj *ct_clone(const CtObj &a);             // a view of the same buffer and level
@@ -264,6 +268,10 @@ CtObj *ev_rescale(Ctx &c, const CtObj &a);
 CtObj *ev_lin_comb(Ctx &c, const std::vector<const CtObj *> &cts, const std::vector<double> &coeffs, double target);
 CtObj *ev_hmult(Ctx &c, const EvkObj &k, const CtObj &a, const CtObj &b);
 CtObj *ev_rotate(Ctx &c, const EvkObj &k, const CtObj &a, int r);
+// up to 16 independent HMults / rotations in one pass of launches (pairs at one level)
+std::vector<CtObj *> ev_hmult_batch(Ctx &c, const EvkObj &k, const std::vector<const CtObj *> &as,
+                                    const std::vector<const CtObj *> &bs);
+std::vector<CtObj *> ev_rotate_batch(Ctx &c, const EvkObj &k, const std::vector<const CtObj *> &as, int r);
 CtObj *ev_rotsum(Ctx &c, const EvkObj &k, const CtObj &a);
 CtObj *ev_drop(Ctx &c, const CtObj &a, int level);
 uint64_t galois_elt(const Ctx &c, int r);

@@ -3,7 +3,7 @@
 // limbs 0..level valid); an extended polynomial is [L+1+K][N] with rows
 // q_0..q_level then p_0..p_{K-1}; a switching key is [dnum][2][L+1+K][N] with
 // rows q_0..q_L, p_0..p_{K-1} (row index = global prime index).
-#include "ctx.cuh"
+#include "ntt.cuh"
 
 namespace ppst {
 
@@ -419,8 +419,9 @@ void k_lincomb(Ctx &c, const LinArgs &args, int level, CtObj &out)
 
 // ---------------------------------------------------------------------------
 // Galois automorphism X -> X^g in the evaluation domain: a permutation.
-// Word k holds a(psi^(2 brv(k) + 1)); sigma_g(a) there equals a at
-// psi^(g (2 brv(k) + 1)), i.e. word brv(((2 brv(k) + 1) g mod 2N - 1) / 2).
+// Natural word n holds a(psi^(2 brv(n) + 1)); sigma_g(a) there equals a at
+// psi^(g (2 brv(n) + 1)), i.e. natural word brv(((2 brv(n) + 1) g mod 2N - 1) / 2).
+// Storage addresses map to natural words by eval_natural / eval_address.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(EW_THREADS) k_automorph_kernel(const uint64_t *__restrict__ in,
                                                                  uint64_t *__restrict__ out, int logN, int nl,
@@ -430,9 +431,10 @@ __global__ void __launch_bounds__(EW_THREADS) k_automorph_kernel(const uint64_t 
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     const int row = blockIdx.y, poly = row / nl, i = row - poly * nl;
-    const uint32_t bk = __brev((uint32_t)k) >> (32 - logN);
+    const uint32_t n = eval_natural((uint32_t)k, logN);  // storage address -> natural position
+    const uint32_t bk = __brev(n) >> (32 - logN);
     const uint64_t e = ((2ull * bk + 1) * g) & (2ull * N - 1);
-    const uint32_t src = __brev((uint32_t)((e - 1) >> 1)) >> (32 - logN);
+    const uint32_t src = eval_address(__brev((uint32_t)((e - 1) >> 1)) >> (32 - logN), logN);
     const size_t base = (size_t)poly * pstride + (size_t)i * N;
     out[base + k] = in[base + src];
 }

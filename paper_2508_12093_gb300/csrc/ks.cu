@@ -1,4 +1,4 @@
-// ks.cu -- fused hybrid key switching (the HMult and rotation hot path).
+// ks.cu -- fused, batched hybrid key switching (the HMult and rotation hot path).
 //
 // Key switching of d (level l, dnum digits of alpha primes, K special primes)
 // is computed as three fused stages, none of which writes an evaluation-domain
@@ -9,10 +9,10 @@
 //      of the COLS transform pass computes the base conversion
 //      sum_i y_i (Q_j / q_i) mod t_e on the fly (the digit's alpha limbs stay in
 //      L2), then runs the pass;
-//   3. k_inner_chunks: one block per (target limb e, 16 chunks) loops over the
-//      digits, finishes the transform in registers (the digit's own limbs are
-//      taken from d in the evaluation domain instead) and accumulates both key
-//      polynomials; the twiddles of prime e are reused by every digit.
+//   3. k_inner_chunks: one block per (item, target limb e, 16 chunks) loops over
+//      the digits, finishes the transform in registers (the digit's own limbs
+//      are taken from d in the evaluation domain instead) and accumulates both
+//      key polynomials; the twiddles of prime e are reused by every digit.
 // ModDown (and, in HMult, the rescale after it) is fused the same way. For
 // limb i < l of the HMult output:
 //   out_i = (d_i + acc_i P^-1 - NTT(conv_i P^-1 + [top]_centred mod q_i)) q_l^-1
@@ -22,9 +22,84 @@
 //   top = INTT(d_l + acc_l P^-1) - conv_l P^-1.
 // All values are exact residues: results are bit-identical to the unfused
 // sequence (tensor, ModUp, NTT, inner product, ModDown, rescale).
+//
+// Batching: up to BMAX independent ciphertexts (same level, same key) go
+// through each stage in one launch. The item is the fastest-varying block
+// index of the inner-product kernel, so the blocks that read the same key
+// tile run back to back and the tile is fetched from HBM once per batch.
 #include "ntt.cuh"
 
 namespace ppst {
+
+constexpr int BMAX = 16;
+
+// per-item ciphertext pointers of a batched launch
+struct ItemPtrs {
+    const uint64_t *in0[BMAX];
+    const uint64_t *in1[BMAX];
+    uint64_t *out[BMAX];
+};
+
+// workspace slices of item `it`
+struct Ws {
+    size_t d2, ext, acc, conv, top;  // item strides in words
+};
+static inline Ws ws_strides(const Ctx &c)
+{
+    const size_t N = c.N, q = c.L + 1, e = c.ext_rows();
+    return Ws{q * N, (size_t)c.dnum * e * N, 2 * e * N, 2 * q * N, 2 * N};
+}
+
+// ---------------------------------------------------------------------------
+// 0. batched tensor / automorphism into the key-switch input buffers
+// ---------------------------------------------------------------------------
+// d0, d1 -> t[item]; d2 -> d2n[item] and d2[item]
+__global__ void __launch_bounds__(256) k_tensor_b(ItemPtrs ip, uint64_t *__restrict__ d2,
+                                                  uint64_t *__restrict__ d2n, const PrimeC *__restrict__ pc, int N,
+                                                  int nl, size_t pstride, size_t d2_stride)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int it = blockIdx.y / nl, i = blockIdx.y - it * nl;
+    const PrimeC p = pc[i];
+    const size_t off = (size_t)i * N + c;
+    const uint64_t *a = ip.in0[it], *b = ip.in1[it];
+    uint64_t *t = ip.out[it];
+    const uint64_t x0 = a[off], x1 = a[pstride + off], y0 = b[off], y1 = b[pstride + off];
+    t[off] = mul_mod(x0, y0, p);
+    const uint64_t v2 = mul_mod(x1, y1, p);
+    d2n[it * d2_stride + off] = v2;
+    d2[it * d2_stride + off] = v2;
+    Acc128 acc{0, 0};
+    mac(acc, x0, y1);
+    mac(acc, x1, y0);
+    t[pstride + off] = mont_mul(mont_redc(acc.hi, acc.lo, p.q, p.qinv), p.r2, p.q, p.qinv);
+}
+
+// sigma_g(c0) -> out[item].c0; sigma_g(c1) -> d2n[item] and d2[item] (evaluation domain permutation)
+__global__ void __launch_bounds__(256) k_automorph_b(ItemPtrs ip, uint64_t *__restrict__ d2,
+                                                     uint64_t *__restrict__ d2n, int logN, int nl, uint64_t g,
+                                                     size_t pstride, size_t d2_stride)
+{
+    const int N = 1 << logN;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int row = blockIdx.y, it = row / (2 * nl), r2 = row - it * 2 * nl, poly = r2 / nl, i = r2 - poly * nl;
+    // output address k holds natural word n; sigma_g moves the evaluation at
+    // psi^(2 brv(n) + 1) from psi^(g (2 brv(n) + 1))
+    const uint32_t n = eval_natural((uint32_t)k, logN);
+    const uint32_t bk = __brev(n) >> (32 - logN);
+    const uint64_t e = ((2ull * bk + 1) * g) & (2ull * N - 1);
+    const uint32_t src = eval_address(__brev((uint32_t)((e - 1) >> 1)) >> (32 - logN), logN);
+    const size_t o = (size_t)i * N;
+    const uint64_t v = ip.in0[it][(size_t)poly * pstride + o + src];
+    if (poly == 0) {
+        ip.out[it][o + k] = v;
+    } else {
+        d2n[it * d2_stride + o + k] = v;
+        d2[it * d2_stride + o + k] = v;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // 2. ModUp fused into the COLS pass
@@ -78,13 +153,15 @@ template <int S, int ALPHA>
 __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
     k_modup_cols(const uint64_t *__restrict__ y, uint64_t *__restrict__ ext, const uint64_t *__restrict__ ks,
                  DigitOffs offs, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN, int level,
-                 int alpha, int L, int K, size_t ext_stride)
+                 int alpha, int L, int K, int nd, size_t ext_stride, Ws ws)
 {
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN, C = N >> S;
     const int E_ext = level + 1 + K;
-    const int j = blockIdx.y / E_ext, e = blockIdx.y - j * E_ext;
+    const int per_item = nd * E_ext;
+    const int it = blockIdx.y / per_item, rem = blockIdx.y - it * per_item;
+    const int j = rem / E_ext, e = rem - j * E_ext;
     const int lo = j * alpha, hi = min(lo + alpha, level + 1), a = hi - lo;
     if (e >= lo && e < hi) return;  // a digit's own limbs come from d itself (block-uniform)
     const int t = e <= level ? e : L + 1 + (e - level - 1);
@@ -96,11 +173,11 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
     pass_coords<S, true>(h, sub);
     const int g = blockIdx.x * P::SUB + sub;
     uint64_t x[P::E];
-    const uint64_t *yl = y + (size_t)lo * N + g;
+    const uint64_t *yl = y + it * ws.d2 + (size_t)lo * N + g;
     if (ALPHA > 0 && a == ALPHA) bconv_words<ALPHA, P::E, P::T>(x, yl, f, a, N, C, h, pt);
     else bconv_words<0, P::E, P::T>(x, yl, f, a, N, C, h, pt);  // a partial last digit
     cols_fwd_core<S>(x, sm, h, sub, tw + (size_t)t * N, pt.q);
-    uint64_t *out = ext + (size_t)j * ext_stride + (size_t)e * N;
+    uint64_t *out = ext + it * ws.ext + (size_t)j * ext_stride + (size_t)e * N;
 #pragma unroll
     for (int k = 0; k < P::E; k++) out[(size_t)(P::E * h + k) * C + g] = x[k];
 }
@@ -112,20 +189,23 @@ template <int S>
 __global__ void __launch_bounds__(PassShape<S>::THREADS, 1)
     k_inner_chunks(const uint64_t *__restrict__ ext, const uint64_t *__restrict__ d2n, const uint64_t *__restrict__ key,
                    uint64_t *__restrict__ acc, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN,
-                   int level, int alpha, int L, int K, int nd, size_t ext_stride)
+                   int level, int alpha, int L, int K, int nd, size_t ext_stride, int B, Ws ws)
 {
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN;
+    const int it = blockIdx.x % B, tile = blockIdx.x / B;
     const int e = blockIdx.y;
     const int row = e <= level ? e : L + 1 + (e - level - 1);
     const PrimeC p = pc[row];
     const Tw *T = tw + (size_t)row * N;
     int h, sub;
     pass_coords<S, false>(h, sub);
-    const int g = blockIdx.x * P::SUB + sub;
+    const int g = tile * P::SUB + sub;
     const size_t krow = (size_t)(L + 1 + K) * N;
-    const size_t fin = (size_t)g * P::M + P::E * h;  // this thread's E words in the store layout
+    // this thread's words (natural E h + k) are stored at fin + T k
+    const size_t fin = (size_t)g * P::M + h;
+    const uint64_t *exti = ext + it * ws.ext, *d2ni = d2n + it * ws.d2;
     uint64_t a0[P::E], a1[P::E];
 #pragma unroll
     for (int k = 0; k < P::E; k++) a0[k] = a1[k] = 0;
@@ -133,15 +213,11 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 1)
         const int lo = j * alpha, hi = min(lo + alpha, level + 1);
         uint64_t x[P::E];
         if (e >= lo && e < hi) {  // block-uniform
-            const uint64_t *src = d2n + (size_t)e * N + fin;
+            const uint64_t *src = d2ni + (size_t)e * N + fin;
 #pragma unroll
-            for (int k = 0; k < P::E; k += 2) {
-                const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(src + k);
-                x[k] = v.x;
-                x[k + 1] = v.y;
-            }
+            for (int k = 0; k < P::E; k++) x[k] = src[P::T * k];
         } else {
-            const uint64_t *src = ext + (size_t)j * ext_stride + (size_t)e * N + (size_t)g * P::M;
+            const uint64_t *src = exti + (size_t)j * ext_stride + (size_t)e * N + (size_t)g * P::M;
 #pragma unroll
             for (int k = 0; k < P::E; k++) x[k] = src[h + P::T * k];
             chunks_fwd_core<S>(x, sm, h, sub, g, N, T, p.q);
@@ -151,20 +227,16 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 1)
         const uint64_t *k0 = key + (size_t)j * 2 * krow + (size_t)row * N + fin;
         const uint64_t *k1 = k0 + krow;
 #pragma unroll
-        for (int k = 0; k < P::E; k += 2) {
-            const ulonglong2 u = *reinterpret_cast<const ulonglong2 *>(k0 + k);
-            const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(k1 + k);
-            a0[k] = add_mod(a0[k], mont_mul(x[k], u.x, p.q, p.qinv), p.q);
-            a0[k + 1] = add_mod(a0[k + 1], mont_mul(x[k + 1], u.y, p.q, p.qinv), p.q);
-            a1[k] = add_mod(a1[k], mont_mul(x[k], v.x, p.q, p.qinv), p.q);
-            a1[k + 1] = add_mod(a1[k + 1], mont_mul(x[k + 1], v.y, p.q, p.qinv), p.q);
+        for (int k = 0; k < P::E; k++) {
+            a0[k] = add_mod(a0[k], mont_mul(x[k], k0[P::T * k], p.q, p.qinv), p.q);
+            a1[k] = add_mod(a1[k], mont_mul(x[k], k1[P::T * k], p.q, p.qinv), p.q);
         }
     }
-    uint64_t *o0 = acc + (size_t)e * N + fin, *o1 = o0 + ext_stride;
+    uint64_t *o0 = acc + it * ws.acc + (size_t)e * N + fin, *o1 = o0 + krow;
 #pragma unroll
-    for (int k = 0; k < P::E; k += 2) {
-        *reinterpret_cast<ulonglong2 *>(o0 + k) = make_ulonglong2(a0[k], a0[k + 1]);
-        *reinterpret_cast<ulonglong2 *>(o1 + k) = make_ulonglong2(a1[k], a1[k + 1]);
+    for (int k = 0; k < P::E; k++) {
+        o0[P::T * k] = a0[k];
+        o1[P::T * k] = a1[k];
     }
 }
 
@@ -172,34 +244,35 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 1)
 // ModDown (+ rescale)
 // ---------------------------------------------------------------------------
 // u_k = d_k[l] + acc_k[l] P^-1 (evaluation domain), the top limb before its inverse transform
-__global__ void k_md_top_kernel(const uint64_t *__restrict__ d, const uint64_t *__restrict__ acc,
-                                uint64_t *__restrict__ top, const PrimeC *__restrict__ pc, Tw pinv, int N, int level,
-                                size_t pstride, size_t ext_stride)
+__global__ void k_md_top_kernel(ItemPtrs ip, const uint64_t *__restrict__ acc, uint64_t *__restrict__ top,
+                                const PrimeC *__restrict__ pc, Tw pinv, int N, int level, size_t pstride,
+                                size_t ext_stride, Ws ws)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
-    const int k = blockIdx.y;
+    const int it = blockIdx.y / 2, k = blockIdx.y - 2 * it;
     const uint64_t q = pc[level].q;
     const size_t o = (size_t)level * N + c;
-    const uint64_t v = csub(shoup(acc[(size_t)k * ext_stride + o], pinv.w, pinv.s, q), q);
-    top[(size_t)k * N + c] = add_mod(d[(size_t)k * pstride + o], v, q);
+    const uint64_t v = csub(shoup(acc[it * ws.acc + (size_t)k * ext_stride + o], pinv.w, pinv.s, q), q);
+    top[it * ws.top + (size_t)k * N + c] = add_mod(ip.in0[it][(size_t)k * pstride + o], v, q);
 }
 
 // top_k -= conv_l(y_k) P^-1 (coefficient domain), y_k = P rows of acc_k after ModDown's first factor
 __global__ void k_md_topfix_kernel(const uint64_t *__restrict__ acc, uint64_t *__restrict__ top,
                                    const uint64_t *__restrict__ hMP, const PrimeC *__restrict__ pc, Tw pinv, int N,
-                                   int level, int L, int K, size_t ext_stride)
+                                   int level, int L, int K, size_t ext_stride, Ws ws)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
-    const int k = blockIdx.y;
+    const int it = blockIdx.y / 2, k = blockIdx.y - 2 * it;
     const PrimeC p = pc[level];
-    const uint64_t *ym = acc + (size_t)k * ext_stride + (size_t)(level + 1) * N + c;
+    const uint64_t *ym = acc + it * ws.acc + (size_t)k * ext_stride + (size_t)(level + 1) * N + c;
     Acc128 a{0, 0};
     for (int m = 0; m < K; m++) mac(a, ym[(size_t)m * N], hMP[(size_t)m * (L + 1) + level]);
     const uint64_t conv = mont_redc(a.hi, a.lo, p.q, p.qinv);
     const uint64_t v = csub(shoup(conv, pinv.w, pinv.s, p.q), p.q);
-    top[(size_t)k * N + c] = sub_mod(top[(size_t)k * N + c], v, p.q);
+    uint64_t *tp = top + it * ws.top + (size_t)k * N + c;
+    *tp = sub_mod(*tp, v, p.q);
 }
 
 // COLS pass of z_i = conv_i(y) P^-1 (+ [top]_centred mod q_i when rescaling), limbs i < nl of both polys
@@ -208,12 +281,13 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
     k_md_cols(const uint64_t *__restrict__ acc, const uint64_t *__restrict__ top, uint64_t *__restrict__ z,
               const uint64_t *__restrict__ hMP, const MdC *__restrict__ mdc, const PrimeC *__restrict__ pc,
               const Tw *__restrict__ tw, int logN, int level, int nl, int L, int K, size_t ext_stride,
-              size_t z_stride)
+              size_t z_stride, Ws ws)
 {
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN, C = N >> S;
-    const int k = blockIdx.y / nl, i = blockIdx.y - k * nl;
+    const int it = blockIdx.y / (2 * nl), rem = blockIdx.y - it * 2 * nl;
+    const int k = rem / nl, i = rem - k * nl;
     const PrimeC p = pc[i];
     const MdC mc = mdc[i];
     __shared__ uint64_t f[16];
@@ -223,8 +297,8 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
     int h, sub;
     pass_coords<S, true>(h, sub);
     const int g = blockIdx.x * P::SUB + sub;
-    const uint64_t *ym = acc + (size_t)k * ext_stride + (size_t)(level + 1) * N + g;
-    const uint64_t *tk = top + (size_t)k * N + g;
+    const uint64_t *ym = acc + it * ws.acc + (size_t)k * ext_stride + (size_t)(level + 1) * N + g;
+    const uint64_t *tk = top + it * ws.top + (size_t)k * N + g;
     uint64_t x[P::E];
     bconv_words<KT, P::E, P::T>(x, ym, f, K, N, C, h, p);
 #pragma unroll
@@ -239,55 +313,56 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
         x[kk] = v;
     }
     cols_fwd_core<S>(x, sm, h, sub, tw + (size_t)i * N, p.q);
-    uint64_t *out = z + (size_t)k * z_stride + (size_t)i * N;
+    uint64_t *out = z + it * ws.conv + (size_t)k * z_stride + (size_t)i * N;
 #pragma unroll
     for (int kk = 0; kk < P::E; kk++) out[(size_t)(P::E * h + kk) * C + g] = x[kk];
 }
 
 // CHUNKS pass of z and the output combine:
-//   RESC:  out_i = d_i q_l^-1 + acc_i (P^-1 q_l^-1) - Z_i q_l^-1
-//   else:  out_i = add_i + acc_i P^-1 - Z_i             (add1 may be null: 0)
+//   RESC:  out_i = d_i q_l^-1 + acc_i (P^-1 q_l^-1) - Z_i q_l^-1     (d = in0[item])
+//   else:  out_i = add_i + acc_i P^-1 - Z_i        (add = in0[item] for c0, 0 for c1)
 template <int S, bool RESC>
 __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
-    k_md_chunks(const uint64_t *__restrict__ z, const uint64_t *__restrict__ acc, const uint64_t *add0,
-                const uint64_t *add1, uint64_t *out0, uint64_t *out1, const MdC *__restrict__ mdc,
-                const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN, int nl, size_t ext_stride,
-                size_t z_stride)
+    k_md_chunks(const uint64_t *__restrict__ z, const uint64_t *__restrict__ acc, ItemPtrs ip,
+                const MdC *__restrict__ mdc, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN, int nl,
+                size_t ext_stride, size_t z_stride, size_t pstride, Ws ws)
 {
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN;
-    const int k = blockIdx.y / nl, i = blockIdx.y - k * nl;
+    const int it = blockIdx.y / (2 * nl), rem = blockIdx.y - it * 2 * nl;
+    const int k = rem / nl, i = rem - k * nl;
     const PrimeC p = pc[i];
     const MdC mc = mdc[i];
     int h, sub;
     pass_coords<S, false>(h, sub);
     const int g = blockIdx.x * P::SUB + sub;
     uint64_t x[P::E];
-    const uint64_t *src = z + (size_t)k * z_stride + (size_t)i * N + (size_t)g * P::M;
+    const uint64_t *src = z + it * ws.conv + (size_t)k * z_stride + (size_t)i * N + (size_t)g * P::M;
 #pragma unroll
     for (int kk = 0; kk < P::E; kk++) x[kk] = src[h + P::T * kk];
     chunks_fwd_core<S>(x, sm, h, sub, g, N, tw + (size_t)i * N, p.q);
-    const size_t fin = (size_t)i * N + (size_t)g * P::M + P::E * h;
-    const uint64_t *ad = k == 0 ? add0 : add1;
-    uint64_t *od = k == 0 ? out0 : out1;
-    const uint64_t *ak = acc + (size_t)k * ext_stride + fin;
+    // natural word E h + kk of the chunk is stored at fin + T kk
+    const size_t fin = (size_t)i * N + (size_t)g * P::M + h;
+    const uint64_t *ad = (RESC || k == 0) ? ip.in0[it] + (size_t)k * pstride : nullptr;
+    uint64_t *od = ip.out[it] + (size_t)k * pstride;
+    const uint64_t *ak = acc + it * ws.acc + (size_t)k * ext_stride + fin;
 #pragma unroll
     for (int kk = 0; kk < P::E; kk++) {
         const uint64_t Z = reduce4q(x[kk], p.q);
-        const uint64_t av = ak[kk];
+        const uint64_t av = ak[P::T * kk];
         uint64_t r;
         if (RESC) {
-            const uint64_t dv = ad[fin + kk];
+            const uint64_t dv = ad[fin + P::T * kk];
             r = csub(shoup(dv, mc.qlinv.w, mc.qlinv.s, p.q), p.q);
             r = add_mod(r, csub(shoup(av, mc.pq.w, mc.pq.s, p.q), p.q), p.q);
             r = sub_mod(r, csub(shoup(Z, mc.qlinv.w, mc.qlinv.s, p.q), p.q), p.q);
         } else {
             r = csub(shoup(av, mc.pinv.w, mc.pinv.s, p.q), p.q);
-            if (ad) r = add_mod(r, ad[fin + kk], p.q);
+            if (ad) r = add_mod(r, ad[fin + P::T * kk], p.q);
             r = sub_mod(r, Z, p.q);
         }
-        od[fin + kk] = r;
+        od[fin + P::T * kk] = r;
     }
 }
 
@@ -296,135 +371,193 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
 // ---------------------------------------------------------------------------
 static dim3 grid_s(const Ctx &c, int S, int rows) { return dim3((c.N >> S) / 16, rows); }
 
-// stages 1-3: d (limbs 0..level) in the evaluation domain in ws_d2n and (as a
-// copy to be transformed) in ws_d2; accumulators to ws_acc
-static void ks_modup_inner(Ctx &c, int level, const Swk &key)
+// stages 1-3 for B items: d (limbs 0..level) of item b in the evaluation domain
+// in ws_d2n[b] and (to be transformed) in ws_d2[b]; accumulators to ws_acc[b]
+static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
 {
+    const Ws ws = ws_strides(c);
     const int nd = c.ndigits(level), E_ext = level + 1 + c.K;
-    ntt_inv_mul(c, map_poly(c, c.ws_d2, level), c.d_modup_outmul + c.modup_outmul_off[level]);
+    LimbMap md{c.ws_d2, ws.d2, level + 1, B, level + 1, 0, 0};
+    ntt_inv_mul(c, md, c.d_modup_outmul + c.modup_outmul_off[level]);
     DigitOffs offs;
     for (int j = 0; j < nd; j++) offs.off[j] = c.modup_off[level][j];
     const size_t es = c.ext_rows() * c.N;
     {
         uint64_t targets = 0;
         for (int j = 0; j < nd; j++) targets += E_ext - (std::min((j + 1) * c.alpha, level + 1) - j * c.alpha);
-        ProfScope _ps(c, "modup_cols", (uint64_t)(level + 1) + targets);  // limbs moved: d read once, targets written
+        ProfScope _ps(c, "modup_cols", (uint64_t)B * ((level + 1) + targets));  // limbs read once + written
         dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
             constexpr int S = decltype(sv)::value;
             dispatch_a(c.alpha, [&](auto av) {
                 constexpr int A = decltype(av)::value;
-                k_modup_cols<S, A><<<grid_s(c, S, nd * E_ext), PassShape<S>::THREADS, 0, c.stream>>>(
-                    c.ws_d2, c.ws_ext, c.d_ks, offs, c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, es);
+                k_modup_cols<S, A><<<grid_s(c, S, B * nd * E_ext), PassShape<S>::THREADS, 0, c.stream>>>(
+                    c.ws_d2, c.ws_ext, c.d_ks, offs, c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, ws);
             });
         });
         check_launch("k_modup_cols");
     }
-    // per target limb: one digit word and two key words per digit read, two accumulators written
-    ProfScope _ps(c, "inner_chunks", (uint64_t)E_ext * (3 * nd + 2));
+    // per target limb and item: one digit word and two key words per digit read,
+    // two accumulators written (the key is counted once per item: the batch
+    // shares its reads through L2)
+    ProfScope _ps(c, "inner_chunks", (uint64_t)B * E_ext * (3 * nd + 2));
     dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
-        k_inner_chunks<S><<<grid_s(c, S, E_ext), PassShape<S>::THREADS, 0, c.stream>>>(
-            c.ws_ext, c.ws_d2n, key.d, c.ws_acc, c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es);
+        const dim3 grid(B * ((c.N >> S) / 16), E_ext);
+        k_inner_chunks<S><<<grid, PassShape<S>::THREADS, 0, c.stream>>>(
+            c.ws_ext, c.ws_d2n, key.d, c.ws_acc, c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, B, ws);
     });
     check_launch("k_inner_chunks");
 }
 
-// ModDown of ws_acc (+ rescale). RESC: out (level-1) = rescale(d + ModDown(acc)),
-// d = the tensor product; else out0 = add0 + ModDown(acc_0), out1 = ModDown(acc_1).
+// ModDown of ws_acc (+ rescale) for B items. RESC: out[b] (level-1) =
+// rescale(in0[b] + ModDown(acc[b])), in0 = the tensor product; else out[b].c0 =
+// in0[b] + ModDown(acc_0), out[b].c1 = ModDown(acc_1).
 template <bool RESC>
-static void ks_moddown(Ctx &c, int level, const uint64_t *d, const uint64_t *add0, uint64_t *out0, uint64_t *out1)
+static void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip)
 {
+    const Ws ws = ws_strides(c);
     const size_t es = c.ext_rows() * c.N, ps = (size_t)(c.L + 1) * c.N;
     const int nl = RESC ? level : level + 1;
     const MdC *mdc = c.d_md_const + (size_t)level * (c.L + 1);
     const MdC &hm = c.md_const[(size_t)level * (c.L + 1) + level];
-    uint64_t *top = c.ws_d2;  // [2][N], free once ModUp has run
+    const dim3 eg(c.N / 256, 2 * B);
     if (RESC) {
-        ProfScope _ps(c, "moddown_top", 6);
-        k_md_top_kernel<<<dim3(c.N / 256, 2), 256, 0, c.stream>>>(d, c.ws_acc, top, c.d_pc, hm.pinv, c.N, level, ps,
-                                                                   es);
+        ProfScope _ps(c, "moddown_top", (uint64_t)6 * B);
+        k_md_top_kernel<<<eg, 256, 0, c.stream>>>(ip, c.ws_acc, c.ws_top, c.d_pc, hm.pinv, c.N, level, ps, es, ws);
         check_launch("k_md_top");
     }
-    // P rows of both accumulators to the coefficient domain, times (P / p_m)^-1
-    LimbMap mp{c.ws_acc + (size_t)(level + 1) * c.N, es, c.K, 2, 0, 0, c.L + 1};
+    // P rows of both accumulators of every item to the coefficient domain, times (P / p_m)^-1
+    LimbMap mp{c.ws_acc + (size_t)(level + 1) * c.N, es, c.K, 2 * B, 0, 0, c.L + 1};
     ntt_inv_mul(c, mp, c.d_md_outmul);
     const uint64_t *hMP = c.d_ks + c.moddown_off + 2 * c.K;
     if (RESC) {
-        LimbMap mt{top, (size_t)c.N, 1, 2, 1, level, 0};
+        LimbMap mt{c.ws_top, (size_t)c.N, 1, 2 * B, 1, level, 0};
         ntt_inv(c, mt);
-        ProfScope _ps(c, "moddown_top", (uint64_t)2 * c.K + 4);
-        k_md_topfix_kernel<<<dim3(c.N / 256, 2), 256, 0, c.stream>>>(c.ws_acc, top, hMP, c.d_pc, hm.pinv, c.N, level,
-                                                                      c.L, c.K, es);
+        ProfScope _ps(c, "moddown_top", (uint64_t)B * (2 * c.K + 4));
+        k_md_topfix_kernel<<<eg, 256, 0, c.stream>>>(c.ws_acc, c.ws_top, hMP, c.d_pc, hm.pinv, c.N, level, c.L, c.K,
+                                                      es, ws);
         check_launch("k_md_topfix");
     }
     {
-        ProfScope _ps(c, "moddown_cols", (uint64_t)2 * c.K + (RESC ? 2 : 0) + 2 * nl);
+        ProfScope _ps(c, "moddown_cols", (uint64_t)B * (2 * c.K + (RESC ? 2 : 0) + 2 * nl));
         dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
             constexpr int S = decltype(sv)::value;
             dispatch_a(c.K, [&](auto kv) {
                 constexpr int KT = decltype(kv)::value;
-                k_md_cols<S, RESC, KT><<<grid_s(c, S, 2 * nl), PassShape<S>::THREADS, 0, c.stream>>>(
-                    c.ws_acc, top, c.ws_conv, hMP, mdc, c.d_pc, c.d_twf, c.logN, level, nl, c.L, c.K, es, ps);
+                k_md_cols<S, RESC, KT><<<grid_s(c, S, B * 2 * nl), PassShape<S>::THREADS, 0, c.stream>>>(
+                    c.ws_acc, c.ws_top, c.ws_conv, hMP, mdc, c.d_pc, c.d_twf, c.logN, level, nl, c.L, c.K, es, ps,
+                    ws);
             });
         });
         check_launch("k_md_cols");
     }
-    ProfScope _ps(c, "moddown_chunks", (uint64_t)(RESC ? 8 : 7) * nl);
+    ProfScope _ps(c, "moddown_chunks", (uint64_t)B * (RESC ? 8 : 7) * nl);
     dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
-        const uint64_t *a0 = RESC ? d : add0;
-        const uint64_t *a1 = RESC ? d + ps : nullptr;
-        k_md_chunks<S, RESC><<<grid_s(c, S, 2 * nl), PassShape<S>::THREADS, 0, c.stream>>>(
-            c.ws_conv, c.ws_acc, a0, a1, out0, out1, mdc, c.d_pc, c.d_twf, c.logN, nl, es, ps);
+        k_md_chunks<S, RESC><<<grid_s(c, S, B * 2 * nl), PassShape<S>::THREADS, 0, c.stream>>>(
+            c.ws_conv, c.ws_acc, ip, mdc, c.d_pc, c.d_twf, c.logN, nl, es, ps, ps, ws);
     });
     check_launch("k_md_chunks");
 }
 
-// HMult: tensor -> key switch of d2 -> add -> rescale, fused as above
-CtObj *ev_hmult(Ctx &c, const EvkObj &k, const CtObj &a, const CtObj &b)
+// HMult of B pairs (each pair at its own min level; all pairs share that level):
+// tensor -> key switch of d2 -> add -> rescale, fused as above
+std::vector<CtObj *> ev_hmult_batch(Ctx &c, const EvkObj &k, const std::vector<const CtObj *> &as,
+                                    const std::vector<const CtObj *> &bs)
 {
-    const int lv = std::min(a.level, b.level);
+    const int B = (int)as.size();
+    if (B < 1 || B > BMAX || bs.size() != as.size()) throw_err(PPST_E_ARG, "hmult batch: 1 to 16 pairs");
+    const int lv = std::min(as[0]->level, bs[0]->level);
+    for (int i = 0; i < B; i++)
+        if (std::min(as[i]->level, bs[i]->level) != lv) throw_err(PPST_E_ARG, "hmult batch: pairs at different levels");
     if (lv < 1) throw_err(PPST_E_DEPTH, "hmult at level 0");
     if (!k.relin.d) throw_err(PPST_E_STATE, "no relinearisation key");
-    ensure_workspace(c);
-    CtObj *t = ct_new(c, lv, a.scale * b.scale);
-    CtObj *o = nullptr;
+    ensure_workspace(c, B);
+    const Ws ws = ws_strides(c);
+    const size_t ps = (size_t)(c.L + 1) * c.N;
+    std::vector<CtObj *> t(B, nullptr), o(B, nullptr);
     try {
-        k_tensor2(c, a, b, lv, t->c0(), t->c1(), c.ws_d2n, c.ws_d2);
-        ks_modup_inner(c, lv, k.relin);
-        o = ct_new(c, lv - 1, (a.scale * b.scale) / (double)c.primes[lv]);
-        ks_moddown<true>(c, lv, t->d, nullptr, o->c0(), o->c1());
+        ItemPtrs ip{};
+        for (int i = 0; i < B; i++) {
+            t[i] = ct_new(c, lv, as[i]->scale * bs[i]->scale);
+            ip.in0[i] = as[i]->d;
+            ip.in1[i] = bs[i]->d;
+            ip.out[i] = t[i]->d;
+        }
+        {
+            ProfScope _ps(c, "tensor", (uint64_t)B * 8 * (lv + 1));
+            k_tensor_b<<<dim3(c.N / 256, B * (lv + 1)), 256, 0, c.stream>>>(ip, c.ws_d2, c.ws_d2n, c.d_pc, c.N,
+                                                                              lv + 1, ps, ws.d2);
+            check_launch("k_tensor_b");
+        }
+        ks_modup_inner(c, lv, k.relin, B);
+        ItemPtrs op{};
+        for (int i = 0; i < B; i++) {
+            o[i] = ct_new(c, lv - 1, (as[i]->scale * bs[i]->scale) / (double)c.primes[lv]);
+            op.in0[i] = t[i]->d;
+            op.out[i] = o[i]->d;
+        }
+        ks_moddown<true>(c, lv, B, op);
     } catch (...) {
-        ct_free(t);
-        ct_free(o);
+        for (CtObj *x : t) ct_free(x);
+        for (CtObj *x : o) ct_free(x);
         throw;
     }
-    ct_free(t);
+    for (CtObj *x : t) ct_free(x);
     return o;
 }
 
-// Rot(r): automorphism of (c0, c1), key switch of the rotated c1
-CtObj *ev_rotate(Ctx &c, const EvkObj &k, const CtObj &a, int r)
+CtObj *ev_hmult(Ctx &c, const EvkObj &k, const CtObj &a, const CtObj &b)
 {
+    return ev_hmult_batch(c, k, {&a}, {&b})[0];
+}
+
+// Rot(r) of B ciphertexts at one level: automorphism of (c0, c1), key switch of the rotated c1
+std::vector<CtObj *> ev_rotate_batch(Ctx &c, const EvkObj &k, const std::vector<const CtObj *> &as, int r)
+{
+    const int B = (int)as.size();
+    if (B < 1 || B > BMAX) throw_err(PPST_E_ARG, "rotate batch: 1 to 16 ciphertexts");
+    const int lv = as[0]->level;
+    for (const CtObj *a : as)
+        if (a->level != lv) throw_err(PPST_E_ARG, "rotate batch: ciphertexts at different levels");
     const int rr = ((r % c.S) + c.S) % c.S;
-    if (rr == 0) return ct_clone(a);
+    std::vector<CtObj *> o(B, nullptr);
+    if (rr == 0) {
+        for (int i = 0; i < B; i++) o[i] = ct_clone(*as[i]);
+        return o;
+    }
     auto it = k.rot.find(rr);
     if (it == k.rot.end()) throw_err(PPST_E_STATE, "no Galois key for rotation " + std::to_string(rr));
-    ensure_workspace(c);
+    ensure_workspace(c, B);
+    const Ws ws = ws_strides(c);
     const size_t ps = (size_t)(c.L + 1) * c.N;
-    CtObj *o = ct_new(c, a.level, a.scale);
     try {
-        // sigma(c0) -> o.c0; sigma(c1) -> ws_d2n, from which ws_d2 is copied
-        k_automorph(c, a.d, a.level, galois_elt(c, rr), o->d, ps, 1);
-        k_automorph(c, a.d + ps, a.level, galois_elt(c, rr), c.ws_d2n, ps, 1);
-        k_copy(c, c.ws_d2, c.ws_d2n, (size_t)(a.level + 1) * c.N);
-        ks_modup_inner(c, a.level, it->second);
-        ks_moddown<false>(c, a.level, nullptr, o->c0(), o->c0(), o->c1());
+        ItemPtrs ip{};
+        for (int i = 0; i < B; i++) {
+            o[i] = ct_new(c, lv, as[i]->scale);
+            ip.in0[i] = as[i]->d;
+            ip.out[i] = o[i]->d;
+        }
+        {
+            ProfScope _ps(c, "automorph", (uint64_t)B * 5 * (lv + 1));
+            k_automorph_b<<<dim3(c.N / 256, B * 2 * (lv + 1)), 256, 0, c.stream>>>(
+                ip, c.ws_d2, c.ws_d2n, c.logN, lv + 1, galois_elt(c, rr), ps, ws.d2);
+            check_launch("k_automorph_b");
+        }
+        ks_modup_inner(c, lv, it->second, B);
+        ItemPtrs op{};
+        for (int i = 0; i < B; i++) {
+            op.in0[i] = o[i]->d;  // sigma(c0), added to ModDown(acc_0) in place
+            op.out[i] = o[i]->d;
+        }
+        ks_moddown<false>(c, lv, B, op);
     } catch (...) {
-        ct_free(o);
+        for (CtObj *x : o) ct_free(x);
         throw;
     }
     return o;
 }
+
+CtObj *ev_rotate(Ctx &c, const EvkObj &k, const CtObj &a, int r) { return ev_rotate_batch(c, k, {&a}, r)[0]; }
 
 }  // namespace ppst

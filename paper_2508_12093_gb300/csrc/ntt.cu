@@ -56,10 +56,9 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCK
 #pragma unroll
     for (int k = 0; k < P::E; k++) x[k] = a[h + P::T * k];
     chunks_fwd_core<S>(x, sm, h, sub, g, N, tw + (size_t)p * N, q);
-    uint64_t *dst = a + P::E * h;
+    // natural word E h + k is stored at h + T k (see eval_address)
 #pragma unroll
-    for (int k = 0; k < P::E; k += 2)
-        *reinterpret_cast<ulonglong2 *>(dst + k) = make_ulonglong2(reduce4q(x[k], q), reduce4q(x[k + 1], q));
+    for (int k = 0; k < P::E; k++) a[h + P::T * k] = reduce4q(x[k], q);
 }
 
 template <int S>
@@ -76,20 +75,15 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCK
     const int g = blockIdx.x * P::SUB + sub;
     uint64_t *a = map.ptr(b, N) + (size_t)g * P::M;
     uint64_t x[P::E];
-    const uint64_t *src = a + P::E * h;
 #pragma unroll
-    for (int k = 0; k < P::E; k += 2) {
-        const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(src + k);
-        x[k] = v.x;
-        x[k + 1] = v.y;
-    }
+    for (int k = 0; k < P::E; k++) x[k] = a[h + P::T * k];  // natural word E h + k
     chunks_inv_core<S>(x, sm, h, sub, g, N, tw + (size_t)p * N, q);
 #pragma unroll
     for (int k = 0; k < P::E; k++) a[h + P::T * k] = x[k];
 }
 
-// last inverse pass; the result is multiplied by N^-1, or by outmul[b] (which
-// then carries N^-1 times a constant of the caller's), and reduced to [0, q)
+// last inverse pass; the result is multiplied by N^-1, or by outmul[i] for limb
+// i of its polynomial (N^-1 times a constant of the caller's), and reduced to [0, q)
 template <int S>
 __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS)
     k_ntt_inv_cols(LimbMap map, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN,
@@ -108,7 +102,7 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCK
 #pragma unroll
     for (int k = 0; k < P::E; k++) x[k] = a[(size_t)(P::E * h + k) * C + g];
     cols_inv_core<S>(x, sm, h, sub, tw + (size_t)p * N, q);
-    const Tw f = outmul ? outmul[b] : Tw{pc[p].ninv, pc[p].ninv_sh};
+    const Tw f = outmul ? outmul[b % map.per_poly] : Tw{pc[p].ninv, pc[p].ninv_sh};
 #pragma unroll
     for (int k = 0; k < P::E; k++) a[(size_t)(h + P::T * k) * C + g] = csub(shoup(x[k], f.w, f.s, q), q);
 }

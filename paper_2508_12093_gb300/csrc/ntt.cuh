@@ -59,6 +59,27 @@ __device__ __forceinline__ Tw ldtw(const Tw *p)
     return Tw{v.x, v.y};
 }
 
+// Storage order of the evaluation domain. The transform's natural output
+// order is bit-reversed (word n holds a(psi^(2 brv(n) + 1))); within each chunk
+// of M = 2^floor(logN/2) words, the word the CHUNKS pass computes at natural
+// position E h + k is stored at h + T k, so that a thread's words are spread
+// with stride T and every evaluation-domain access of the CHUNKS pass (keys,
+// accumulators, outputs) is coalesced across the threads h.
+__host__ __device__ __forceinline__ uint32_t eval_natural(uint32_t a, int logN)
+{
+    const int S = logN / 2, A = (S + 1) / 2;
+    const uint32_t M = 1u << S, E = 1u << A, T = M / E;
+    const uint32_t g = a >> S, r = a & (M - 1), h = r % T, k = r / T;
+    return (g << S) + E * h + k;
+}
+__host__ __device__ __forceinline__ uint32_t eval_address(uint32_t n, int logN)
+{
+    const int S = logN / 2, A = (S + 1) / 2;
+    const uint32_t M = 1u << S, E = 1u << A, T = M / E;
+    const uint32_t g = n >> S, s = n & (M - 1), h = s / E, k = s % E;
+    return (g << S) + h + T * k;
+}
+
 // thread coordinates of a pass: COLS -> (sub = column in block, h), CHUNKS -> (h, sub = chunk in block)
 template <int S, bool COLS>
 __device__ __forceinline__ void pass_coords(int &h, int &sub)

@@ -18,9 +18,13 @@
 // associated (x' y)(y y) (depth 2 per step); padding slots of multi-ciphertext
 // columns are corrected with integer multiples of mu^p.
 #include <cmath>
+#include <condition_variable>
+#include <exception>
 #include <functional>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <thread>
 
 #include "ctx.cuh"
 
@@ -44,27 +48,255 @@ struct Holder {
 };
 typedef std::shared_ptr<Holder> H;
 
+// ---------------------------------------------------------------------------
+// batch scheduler: the queries of a batch run their statistic programs on host
+// threads; each evaluator op is a request. When every live query waits on a
+// request, the scheduler thread (the caller's) executes them: HMults at one
+// level and rotate-and-sums at one level as batched launches (keys read once
+// per batch), the rest one by one. All GPU work is issued by that thread.
+// ---------------------------------------------------------------------------
+enum ReqKind { R_ADD, R_SUB, R_ADDC, R_MULI, R_MULC, R_LINC, R_HMULT, R_ROTSUM };
+
+struct Req {
+    ReqKind kind;
+    const CtObj *a = nullptr, *b = nullptr;
+    std::vector<const CtObj *> xs;
+    std::vector<double> cs;
+    double x = 0, target = 0;
+    int64_t m = 0;
+    CtObj *result = nullptr;
+    std::exception_ptr err;
+    bool done = false;
+};
+
+struct Sched {
+    Ctx &c;
+    const EvkObj &k;
+    std::mutex mu;
+    std::condition_variable cv_sched, cv_work;
+    std::vector<Req *> pending;
+    int total = 0, waiting = 0, finished = 0;
+
+    CtObj *submit(Req &r)
+    {
+        std::unique_lock<std::mutex> lk(mu);
+        pending.push_back(&r);
+        waiting++;
+        cv_sched.notify_one();
+        cv_work.wait(lk, [&] { return r.done; });
+        if (r.err) std::rethrow_exception(r.err);
+        return r.result;
+    }
+
+    void worker_finished()
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        finished++;
+        cv_sched.notify_one();
+    }
+
+    void exec_one(Req &r)
+    {
+        switch (r.kind) {
+        case R_ADD: r.result = ev_add(c, *r.a, *r.b, false); break;
+        case R_SUB: r.result = ev_add(c, *r.a, *r.b, true); break;
+        case R_ADDC: r.result = ev_add_const(c, *r.a, r.x); break;
+        case R_MULI: r.result = ev_mul_int(c, *r.a, r.m); break;
+        case R_MULC: r.result = ev_mul_const(c, *r.a, r.x, r.target); break;
+        case R_LINC: r.result = ev_lin_comb(c, r.xs, r.cs, r.target); break;
+        case R_HMULT: r.result = ev_hmult(c, k, *r.a, *r.b); break;
+        case R_ROTSUM: r.result = ev_rotsum(c, k, *r.a); break;
+        }
+    }
+
+    // HMults grouped by level, at most 16 per launch sequence
+    void exec_hmults(std::vector<Req *> &rs)
+    {
+        std::map<int, std::vector<Req *>> by;
+        for (Req *r : rs) by[std::min(r->a->level, r->b->level)].push_back(r);
+        for (auto &kv : by) {
+            for (size_t s = 0; s < kv.second.size(); s += 16) {
+                std::vector<Req *> g(kv.second.begin() + s, kv.second.begin() + std::min(s + 16, kv.second.size()));
+                std::vector<const CtObj *> as, bs;
+                for (Req *r : g) {
+                    as.push_back(r->a);
+                    bs.push_back(r->b);
+                }
+                std::vector<CtObj *> out = ev_hmult_batch(c, k, as, bs);
+                for (size_t i = 0; i < g.size(); i++) g[i]->result = out[i];
+            }
+        }
+    }
+
+    // rotate-and-sums grouped by level: step s rotates every member by 2^s in one batch
+    void exec_rotsums(std::vector<Req *> &rs)
+    {
+        std::map<int, std::vector<Req *>> by;
+        for (Req *r : rs) by[r->a->level].push_back(r);
+        for (auto &kv : by) {
+            for (size_t s = 0; s < kv.second.size(); s += 16) {
+                std::vector<Req *> g(kv.second.begin() + s, kv.second.begin() + std::min(s + 16, kv.second.size()));
+                std::vector<CtObj *> acc;
+                for (Req *r : g) acc.push_back(ct_clone(*r->a));
+                try {
+                    for (int st = 0; st < c.logN - 1; st++) {
+                        std::vector<const CtObj *> in(acc.begin(), acc.end());
+                        std::vector<CtObj *> rot = ev_rotate_batch(c, k, in, 1 << st);
+                        for (size_t i = 0; i < g.size(); i++) {
+                            CtObj *sum = nullptr;
+                            try {
+                                sum = ev_add(c, *acc[i], *rot[i], false);
+                            } catch (...) {
+                                for (CtObj *x : rot) ct_free(x);
+                                throw;
+                            }
+                            ct_free(acc[i]);
+                            acc[i] = sum;
+                        }
+                        for (CtObj *x : rot) ct_free(x);
+                    }
+                } catch (...) {
+                    for (CtObj *x : acc) ct_free(x);
+                    throw;
+                }
+                for (size_t i = 0; i < g.size(); i++) g[i]->result = acc[i];
+            }
+        }
+    }
+
+    void exec_pending(std::vector<Req *> &batch)
+    {
+        std::vector<Req *> hm, rsum;
+        for (Req *r : batch) {
+            if (r->kind == R_HMULT) hm.push_back(r);
+            else if (r->kind == R_ROTSUM) rsum.push_back(r);
+        }
+        auto guarded = [&](std::vector<Req *> &group, auto fn) {
+            try {
+                fn(group);
+            } catch (...) {  // a failed batch: run its members one by one to attribute errors
+                for (Req *r : group) {
+                    if (r->result) continue;
+                    try {
+                        exec_one(*r);
+                    } catch (...) {
+                        r->err = std::current_exception();
+                    }
+                }
+            }
+        };
+        if (!hm.empty()) guarded(hm, [&](std::vector<Req *> &g) { exec_hmults(g); });
+        if (!rsum.empty()) guarded(rsum, [&](std::vector<Req *> &g) { exec_rotsums(g); });
+        for (Req *r : batch) {
+            if (r->kind == R_HMULT || r->kind == R_ROTSUM) continue;
+            try {
+                exec_one(*r);
+            } catch (...) {
+                r->err = std::current_exception();
+            }
+        }
+    }
+
+    // scheduler loop: run until every worker has finished
+    void run()
+    {
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            cv_sched.wait(lk, [&] { return waiting + finished == total; });
+            if (pending.empty()) {
+                if (finished == total) return;
+                continue;
+            }
+            std::vector<Req *> batch;
+            batch.swap(pending);
+            lk.unlock();
+            exec_pending(batch);
+            lk.lock();
+            for (Req *r : batch) r->done = true;
+            waiting -= (int)batch.size();
+            cv_work.notify_all();
+        }
+    }
+};
+
 struct Ev {
     Ctx &c;
     const EvkObj &k;
+    Sched *sched = nullptr;  // batched mode: ops go through the scheduler
     H w(CtObj *p) { return std::make_shared<Holder>(p); }
     int level(const H &a) const { return a->ct->level; }
     double scale(const H &a) const { return a->ct->scale; }
     uint64_t prime(int l) const { return c.primes[l]; }
-    H add(const H &a, const H &b) { return w(ev_add(c, *a->ct, *b->ct, false)); }
-    H sub(const H &a, const H &b) { return w(ev_add(c, *a->ct, *b->ct, true)); }
-    H add_const(const H &a, double x) { return w(ev_add_const(c, *a->ct, x)); }
-    H mul_int(const H &a, int64_t m) { return w(ev_mul_int(c, *a->ct, m)); }
-    H mul_const(const H &a, double x, double target = 0) { return w(ev_mul_const(c, *a->ct, x, target)); }
-    H hmult(const H &a, const H &b) { return w(ev_hmult(c, k, *a->ct, *b->ct)); }
+    H req(Req &r) { return w(sched->submit(r)); }
+    H add(const H &a, const H &b)
+    {
+        if (!sched) return w(ev_add(c, *a->ct, *b->ct, false));
+        Req r{R_ADD};
+        r.a = a->ct;
+        r.b = b->ct;
+        return req(r);
+    }
+    H sub(const H &a, const H &b)
+    {
+        if (!sched) return w(ev_add(c, *a->ct, *b->ct, true));
+        Req r{R_SUB};
+        r.a = a->ct;
+        r.b = b->ct;
+        return req(r);
+    }
+    H add_const(const H &a, double x)
+    {
+        if (!sched) return w(ev_add_const(c, *a->ct, x));
+        Req r{R_ADDC};
+        r.a = a->ct;
+        r.x = x;
+        return req(r);
+    }
+    H mul_int(const H &a, int64_t m)
+    {
+        if (!sched) return w(ev_mul_int(c, *a->ct, m));
+        Req r{R_MULI};
+        r.a = a->ct;
+        r.m = m;
+        return req(r);
+    }
+    H mul_const(const H &a, double x, double target = 0)
+    {
+        if (!sched) return w(ev_mul_const(c, *a->ct, x, target));
+        Req r{R_MULC};
+        r.a = a->ct;
+        r.x = x;
+        r.target = target;
+        return req(r);
+    }
+    H hmult(const H &a, const H &b)
+    {
+        if (!sched) return w(ev_hmult(c, k, *a->ct, *b->ct));
+        Req r{R_HMULT};
+        r.a = a->ct;
+        r.b = b->ct;
+        return req(r);
+    }
     H lin_comb(const std::vector<H> &xs, const std::vector<double> &cs, double target)
     {
         std::vector<const CtObj *> p;
         for (const H &x : xs) p.push_back(x->ct);
-        return w(ev_lin_comb(c, p, cs, target));
+        if (!sched) return w(ev_lin_comb(c, p, cs, target));
+        Req r{R_LINC};
+        r.xs = p;
+        r.cs = cs;
+        r.target = target;
+        return req(r);
     }
+    // a level view: no GPU work, safe on any thread
     H drop(const H &a, int l) { return l == a->ct->level ? a : w(ev_drop(c, *a->ct, l)); }
-    H rotsum(const H &a) { return w(ev_rotsum(c, k, *a->ct)); }
+    H rotsum(const H &a)
+    {
+        if (!sched) return w(ev_rotsum(c, k, *a->ct));
+        Req r{R_ROTSUM};
+        r.a = a->ct;
+        return req(r);
+    }
 };
 
 // ---- Chebyshev interpolation (Sec. 3.4, Eq. 1, 3, 4) ----
@@ -312,32 +544,70 @@ Col view(const ColObj &col)
     return out;
 }
 
+ResObj *run_one(Ev &ev, const QueryIn &q)
+{
+    const int kk = q.o.cheb_log2deg, tt = q.o.newton_steps;
+    Col x = view(*q.x);
+    const size_t n = q.x->n;
+    Col res;
+    switch (q.stat) {
+    case PPST_ZSCORE: res = znorm(ev, x, n, q.o.B_x, kk, tt); break;
+    case PPST_KURT: res.push_back(kurt(ev, x, n, q.o.B_x, kk, tt)); break;
+    case PPST_SKEW: res.push_back(skew(ev, x, n, q.o.B_x, kk, tt)); break;
+    case PPST_CV: res.push_back(cv(ev, x, n, q.o.B_x, kk, tt)); break;
+    case PPST_PCC: res.push_back(pcc(ev, x, view(*q.y), n, q.o.B_x, q.o.B_y, kk, tt)); break;
+    default: throw_err(PPST_E_ARG, "unknown statistic");
+    }
+    ResObj *r = new ResObj();
+    r->ctx = &ev.c;
+    r->stat = q.stat;
+    r->n = n;
+    r->level_in = q.x->cts[0]->level;
+    for (H &h : res) r->cts.push_back(h->release());
+    return r;
+}
+
+void free_res(ResObj *r)
+{
+    if (!r) return;
+    for (CtObj *ct : r->cts) ct_free(ct);
+    delete r;
+}
+
 }  // namespace
 
 void run_queries(Ctx &c, const EvkObj &k, const std::vector<QueryIn> &qs, std::vector<ResObj *> &out)
 {
-    Ev ev{c, k};
-    for (const QueryIn &q : qs) {
-        const int kk = q.o.cheb_log2deg, tt = q.o.newton_steps;
-        Col x = view(*q.x);
-        const size_t n = q.x->n;
-        Col res;
-        switch (q.stat) {
-        case PPST_ZSCORE: res = znorm(ev, x, n, q.o.B_x, kk, tt); break;
-        case PPST_KURT: res.push_back(kurt(ev, x, n, q.o.B_x, kk, tt)); break;
-        case PPST_SKEW: res.push_back(skew(ev, x, n, q.o.B_x, kk, tt)); break;
-        case PPST_CV: res.push_back(cv(ev, x, n, q.o.B_x, kk, tt)); break;
-        case PPST_PCC: res.push_back(pcc(ev, x, view(*q.y), n, q.o.B_x, q.o.B_y, kk, tt)); break;
-        default: throw_err(PPST_E_ARG, "unknown statistic");
-        }
-        ResObj *r = new ResObj();
-        r->ctx = &c;
-        r->stat = q.stat;
-        r->n = n;
-        r->level_in = q.x->cts[0]->level;
-        for (H &h : res) r->cts.push_back(h->release());
-        out.push_back(r);
+    if (qs.size() <= 1) {
+        Ev ev{c, k};
+        for (const QueryIn &q : qs) out.push_back(run_one(ev, q));
+        return;
     }
+    Sched sched{c, k};
+    sched.total = (int)qs.size();
+    std::vector<ResObj *> res(qs.size(), nullptr);
+    std::vector<std::exception_ptr> errs(qs.size());
+    std::vector<std::thread> th;
+    for (size_t i = 0; i < qs.size(); i++) {
+        th.emplace_back([&, i] {
+            try {
+                Ev ev{c, k, &sched};
+                res[i] = run_one(ev, qs[i]);
+            } catch (...) {
+                errs[i] = std::current_exception();
+            }
+            sched.worker_finished();
+        });
+    }
+    sched.run();
+    for (std::thread &t : th) t.join();
+    for (size_t i = 0; i < qs.size(); i++) {
+        if (errs[i]) {
+            for (ResObj *r : res) free_res(r);
+            std::rethrow_exception(errs[i]);
+        }
+    }
+    for (ResObj *r : res) out.push_back(r);
 }
 
 }  // namespace ppst

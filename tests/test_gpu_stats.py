@@ -168,6 +168,41 @@ def test_multi_ciphertext_column_full_size(big):
     assert np.abs(z - ref["znorm"]).max() / np.abs(ref["znorm"]).max() < TOL
 
 
+def test_batch_full_size(big):
+    """Twelve mixed queries over six columns of uneven lengths (the batched
+    workload's shape) as one batch: every result identical to the query run
+    alone, and within 1e-3 of FP64."""
+    from oracle import stats as ost
+    ctx, sk, evk = big
+    lens = workloads.log_uniform_lengths(6, 1024, 32768, seed=7)
+    cols, data = [], []
+    for i, n in enumerate(lens):
+        if i % 2 == 0:
+            x = workloads.lognormal_column(int(n), seed=10 + i)
+            data.append((x, None))
+            cols.append((ctx.encrypt_column(evk, x, 20 + i), None))
+        else:
+            x, y = workloads.pcc_pair(int(n), seed=10 + i)
+            data.append((x, y))
+            cols.append((ctx.encrypt_column(evk, x, 20 + i), ctx.encrypt_column(evk, y, 40 + i)))
+    qs = []
+    for (cx, cy), (x, y) in zip(cols, data):
+        if cy is None:
+            qs += [("skew", cx, None, OPTS16), ("kurt", cx, None, OPTS16)]
+        else:
+            qs += [("pcc", cx, cy, dict(OPTS16, B_x=1.0)), ("cv", cy, None, OPTS16)]
+    batch = ctx.query_batch(evk, qs)
+    for q, rb in zip(qs, batch):
+        rs = ctx.query(evk, q[0], q[1], q[2], q[3])
+        a, b = ctx.ct_export(rb.cts()[0]), ctx.ct_export(rs.cts()[0])
+        assert a[2:] == b[2:] and np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), q[0]
+    for i, ((x, y), rb) in enumerate(zip([d for d in data for _ in range(2)], batch)):
+        name = qs[i][0]
+        ref = ost.plain_stats(y, None)["cv"] if name == "cv" else ost.plain_stats(x, y)[name]
+        v, _ = ctx.decrypt(sk, rb)
+        assert abs(v[0] / ref - 1) < TOL, (name, v[0], ref)
+
+
 def test_hmult_full_size_matches_oracle():
     """HMult + key switch at N = 2^16, top level (24 limbs, dnum = 6): limbs
     bit-exact against the oracle on shared keys and ciphertexts."""
