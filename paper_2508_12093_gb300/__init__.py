@@ -117,6 +117,46 @@ def _opts(o):
                       int(o.get("newton_steps", 3)))
 
 
+class Server(_Handle):
+    """Continuous-batching request loop over one context and key set.
+
+    Queries join the running schedule at the next evaluator-op boundary, so
+    their HMults and rotate-and-sums share batched key-switch launches with
+    the queries already in flight. Admission is bounded by an HBM budget and a
+    maximum number of concurrent queries."""
+
+    def __init__(self, ctx, evk, hbm_budget, max_batch=16):
+        out = ctypes.c_void_p()
+        ctx._check(lib.ppst_server_create(ctx.ptr, evk.ptr, int(hbm_budget), int(max_batch), ctypes.byref(out)))
+        super().__init__(ctx, out.value)
+        self.evk = evk
+        self._rows = {}
+
+    def submit(self, stat, x, y=None, opts=None):
+        t = _lib.c_u64()
+        o = _opts(opts)
+        self.ctx._check(lib.ppst_submit(self.ptr, STATS.get(stat, stat), x.ptr, y.ptr if y is not None else None,
+                                        ctypes.byref(o), ctypes.byref(t)))
+        self._rows[t.value] = x.n if STATS.get(stat, stat) == PPST_ZSCORE else 1
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        """The ticket's Result, or None on timeout (the ticket stays valid)."""
+        out = ctypes.c_void_p()
+        rc = lib.ppst_wait(self.ptr, ticket, int(timeout_ms), ctypes.byref(out))
+        if rc == -7:  # PPST_E_TIMEOUT
+            return None
+        self.ctx._check(rc)
+        r = Result(self.ctx, out.value)
+        r.n = self._rows.pop(ticket)
+        return r
+
+    def latency(self, ticket):
+        s = ctypes.c_double()
+        self.ctx._check(lib.ppst_ticket_latency(self.ptr, ticket, ctypes.byref(s)))
+        return s.value
+
+
 class Context:
     """One parameter set on one GPU stream (not thread-safe)."""
 

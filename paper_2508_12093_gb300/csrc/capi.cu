@@ -3,7 +3,6 @@
 #include <new>
 
 #include "ctx.cuh"
-#include "serve.cuh"
 
 using namespace ppst;
 
@@ -13,8 +12,10 @@ template <class F>
 int guard(Ctx *c, F &&f)
 {
     try {
+        std::unique_lock<std::recursive_mutex> lk;
+        if (c) lk = std::unique_lock<std::recursive_mutex>(c->exec_mu);
         f();
-        if (c) c->err = Error{0, ""};
+        if (c) c->clear_err();
         return PPST_OK;
     } catch (const PpstError &e) {
         if (c) c->fail(e.code, e.msg);
@@ -50,6 +51,22 @@ void check_opts(const ppst_qopts &o, int stat)
 }
 
 }  // namespace
+
+namespace ppst {
+void validate_query(const Ctx &cc, const QueryIn &q)
+{
+    const Ctx *c = &cc;
+    REQ(q.stat >= PPST_ZSCORE && q.stat <= PPST_PCC, "unknown statistic");
+    REQ(ok(q.x, TAG_COL) && q.x->ctx == c, "bad column");
+    if (q.stat == PPST_PCC) {
+        REQ(ok(q.y, TAG_COL) && q.y->ctx == c && q.y->n == q.x->n && q.y->cts.size() == q.x->cts.size(),
+            "PCC needs a second column of the same length");
+        REQ(q.y->cts[0]->level == q.x->cts[0]->level, "PCC columns at different levels");
+    }
+    for (const CtObj *ct : q.x->cts) REQ(ct->level == q.x->cts[0]->level, "column ciphertexts at mixed levels");
+    check_opts(q.o, q.stat);
+}
+}  // namespace ppst
 
 extern "C" {
 
@@ -245,7 +262,7 @@ int ppst_decrypt_ct(ppst_ctx *ctx, const ppst_sk *sk, const ppst_ct *ct, double 
 }
 
 static void run_checked(Ctx *c, const EvkObj *k, size_t count, const ppst_stat *stats, const ppst_col *const *xs,
-                        const ppst_col *const *ys, const ppst_qopts *opts, ppst_res **outs)
+                 const ppst_col *const *ys, const ppst_qopts *opts, ppst_res **outs)
 {
     REQ(ok(k, TAG_EVK) && k->ctx == c && stats && xs && outs, "bad arguments");
     std::vector<QueryIn> qs;
@@ -256,15 +273,7 @@ static void run_checked(Ctx *c, const EvkObj *k, size_t count, const ppst_stat *
         q.x = (const ColObj *)xs[i];
         q.y = ys ? (const ColObj *)ys[i] : nullptr;
         q.o = opts ? opts[i] : default_opts;
-        REQ(q.stat >= PPST_ZSCORE && q.stat <= PPST_PCC, "unknown statistic");
-        REQ(ok(q.x, TAG_COL) && q.x->ctx == c, "bad column");
-        if (q.stat == PPST_PCC) {
-            REQ(ok(q.y, TAG_COL) && q.y->ctx == c && q.y->n == q.x->n && q.y->cts.size() == q.x->cts.size(),
-                "PCC needs a second column of the same length");
-            REQ(q.y->cts[0]->level == q.x->cts[0]->level, "PCC columns at different levels");
-        }
-        for (const CtObj *ct : q.x->cts) REQ(ct->level == q.x->cts[0]->level, "column ciphertexts at mixed levels");
-        check_opts(q.o, q.stat);
+        validate_query(*c, q);
         qs.push_back(q);
     }
     std::vector<ResObj *> res;

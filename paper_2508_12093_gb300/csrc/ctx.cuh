@@ -1,5 +1,6 @@
 // ctx.cuh -- context, handles and internal entry points of the library.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -110,7 +111,7 @@ struct Prof {
     std::string only;  // "" = every class
     std::vector<cudaEvent_t> spare;
     std::map<std::string, std::vector<ProfRec>> rec;
-    uint64_t launches = 0;  // kernel launches issued by this context (always counted)
+    std::atomic<uint64_t> launches{0};  // kernel launches issued by this context (always counted)
     cudaEvent_t take();
 };
 
@@ -146,6 +147,10 @@ struct Ctx {
     cudaStream_t stream = nullptr;
     Pool pool;
     Error err{0, ""};
+    std::mutex err_mu;  // server threads may record errors concurrently
+    // Held while GPU work is issued (each ABI call; each scheduling round of a
+    // server), so that a server and direct calls never share the workspace at once.
+    std::recursive_mutex exec_mu;
     // workspace (allocated on first key switch)
     // (each with a leading item dimension of ws_items for batched key switching)
     uint64_t *ws_d2 = nullptr;   // [L+1][N]
@@ -160,8 +165,14 @@ struct Ctx {
     size_t ct_words() const { return (size_t)2 * (L + 1) * N; }
     size_t ext_rows() const { return (size_t)(L + 1 + K); }
     int ndigits(int level) const { return (level + 1 + alpha - 1) / alpha; }
+    void clear_err()
+    {
+        std::lock_guard<std::mutex> lk(err_mu);
+        err = Error{0, ""};
+    }
     int fail(int code, const std::string &m)
     {
+        std::lock_guard<std::mutex> lk(err_mu);
         err.code = code;
         err.msg = m;
         return code;
@@ -292,5 +303,10 @@ struct QueryIn {
     ppst_qopts o;
 };
 void run_queries(Ctx &c, const EvkObj &k, const std::vector<QueryIn> &qs, std::vector<ResObj *> &out);
+void validate_query(const Ctx &c, const QueryIn &q);  // PPST_E_ARG on a malformed query
+
+// ---- serving (stats.cu) ----
+struct Server;
+void server_destroy(Server *s);
 
 }  // namespace ppst

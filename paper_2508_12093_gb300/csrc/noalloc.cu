@@ -118,8 +118,9 @@ extern "C" int ppst_hmult_noalloc(ppst_ctx *ctx, const ppst_evk *evk, const ppst
     if (O == A || O == B || O->buf.use_count() != 1)
         return c->fail(PPST_E_ARG, "the output must own its buffer alone (not an input, not a level view)");
     try {
+        std::lock_guard<std::recursive_mutex> lk(c->exec_mu);  // the workspace pointers are swapped meanwhile
         hmult_noalloc(*c, *k, *A, *B, *O);
-        c->err = Error{0, ""};
+        c->clear_err();
         return PPST_OK;
     } catch (const PpstError &e) {
         return c->fail(e.code, e.msg);

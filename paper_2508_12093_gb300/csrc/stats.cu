@@ -17,8 +17,10 @@
 // to a common scale so that all Adds see equal scales; Newton's products are
 // associated (x' y)(y y) (depth 2 per step); padding slots of multi-ciphertext
 // columns are corrected with integer multiples of mu^p.
+#include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <deque>
 #include <exception>
 #include <functional>
 #include <map>
@@ -67,7 +69,36 @@ struct Req {
     CtObj *result = nullptr;
     std::exception_ptr err;
     bool done = false;
+    bool last = true;  // last request of one worker's submission
 };
+
+// HMults grouped by level, at most 16 per launch sequence; results in input order
+std::vector<CtObj *> hmult_grouped(Ctx &c, const EvkObj &k, const std::vector<const CtObj *> &a,
+                                   const std::vector<const CtObj *> &b)
+{
+    std::vector<CtObj *> out(a.size(), nullptr);
+    std::map<int, std::vector<size_t>> by;
+    for (size_t i = 0; i < a.size(); i++) by[std::min(a[i]->level, b[i]->level)].push_back(i);
+    try {
+        for (auto &kv : by) {
+            const std::vector<size_t> &ix = kv.second;
+            for (size_t s = 0; s < ix.size(); s += 16) {
+                std::vector<const CtObj *> as, bs;
+                for (size_t j = s; j < std::min(s + 16, ix.size()); j++) {
+                    as.push_back(a[ix[j]]);
+                    bs.push_back(b[ix[j]]);
+                }
+                std::vector<CtObj *> r = ev_hmult_batch(c, k, as, bs);
+                for (size_t j = 0; j < r.size(); j++) out[ix[s + j]] = r[j];
+            }
+        }
+    } catch (...) {
+        for (CtObj *x : out)
+            if (x) ct_free(x);
+        throw;
+    }
+    return out;
+}
 
 struct Sched {
     Ctx &c;
@@ -75,7 +106,9 @@ struct Sched {
     std::mutex mu;
     std::condition_variable cv_sched, cv_work;
     std::vector<Req *> pending;
-    int total = 0, waiting = 0, finished = 0;
+    int active = 0, waiting = 0;  // live workers; workers blocked on a request
+    bool stop = false;
+    uint64_t rounds = 0;          // scheduling rounds executed
 
     CtObj *submit(Req &r)
     {
@@ -88,10 +121,41 @@ struct Sched {
         return r.result;
     }
 
+    // independent requests of one worker, executed in one round (same-level
+    // HMults share launches); the first error is rethrown after all finished
+    void submit_many(std::vector<Req> &rs)
+    {
+        if (rs.empty()) return;
+        std::unique_lock<std::mutex> lk(mu);
+        for (Req &r : rs) {
+            r.last = false;
+            pending.push_back(&r);
+        }
+        rs.back().last = true;
+        waiting++;
+        cv_sched.notify_one();
+        cv_work.wait(lk, [&] { return rs.back().done; });
+        for (Req &r : rs)
+            if (r.err) std::rethrow_exception(r.err);
+    }
+
+    void worker_started()
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        active++;
+    }
+
     void worker_finished()
     {
         std::lock_guard<std::mutex> lk(mu);
-        finished++;
+        active--;
+        cv_sched.notify_one();
+    }
+
+    void request_stop()
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        stop = true;
         cv_sched.notify_one();
     }
 
@@ -109,23 +173,15 @@ struct Sched {
         }
     }
 
-    // HMults grouped by level, at most 16 per launch sequence
     void exec_hmults(std::vector<Req *> &rs)
     {
-        std::map<int, std::vector<Req *>> by;
-        for (Req *r : rs) by[std::min(r->a->level, r->b->level)].push_back(r);
-        for (auto &kv : by) {
-            for (size_t s = 0; s < kv.second.size(); s += 16) {
-                std::vector<Req *> g(kv.second.begin() + s, kv.second.begin() + std::min(s + 16, kv.second.size()));
-                std::vector<const CtObj *> as, bs;
-                for (Req *r : g) {
-                    as.push_back(r->a);
-                    bs.push_back(r->b);
-                }
-                std::vector<CtObj *> out = ev_hmult_batch(c, k, as, bs);
-                for (size_t i = 0; i < g.size(); i++) g[i]->result = out[i];
-            }
+        std::vector<const CtObj *> as, bs;
+        for (Req *r : rs) {
+            as.push_back(r->a);
+            bs.push_back(r->b);
         }
+        std::vector<CtObj *> out = hmult_grouped(c, k, as, bs);
+        for (size_t i = 0; i < rs.size(); i++) rs[i]->result = out[i];
     }
 
     // rotate-and-sums grouped by level: step s rotates every member by 2^s in one batch
@@ -197,23 +253,29 @@ struct Sched {
         }
     }
 
-    // scheduler loop: run until every worker has finished
-    void run()
+    // Scheduler loop. A round runs when every live worker waits on a request:
+    // workers that join meanwhile (continuous batching) are part of the next
+    // round. forever = false: return once no worker is left; forever = true:
+    // keep serving until request_stop() with no worker left.
+    void run(bool forever)
     {
         std::unique_lock<std::mutex> lk(mu);
         for (;;) {
-            cv_sched.wait(lk, [&] { return waiting + finished == total; });
-            if (pending.empty()) {
-                if (finished == total) return;
-                continue;
-            }
+            cv_sched.wait(lk, [&] { return (active > 0 && waiting == active) || (active == 0 && (!forever || stop)); });
+            if (active == 0) return;
             std::vector<Req *> batch;
             batch.swap(pending);
             lk.unlock();
-            exec_pending(batch);
+            {
+                std::lock_guard<std::recursive_mutex> g(c.exec_mu);
+                exec_pending(batch);
+            }
             lk.lock();
-            for (Req *r : batch) r->done = true;
-            waiting -= (int)batch.size();
+            rounds++;
+            for (Req *r : batch) {
+                r->done = true;
+                waiting -= r->last ? 1 : 0;
+            }
             cv_work.notify_all();
         }
     }
@@ -288,6 +350,74 @@ struct Ev {
         r.target = target;
         return req(r);
     }
+    // ---- independent ops over the ciphertexts of a column: one scheduling round ----
+    std::vector<H> run_many(std::vector<Req> &rs)
+    {
+        sched->submit_many(rs);
+        std::vector<H> out;
+        for (Req &r : rs) out.push_back(w(r.result));
+        return out;
+    }
+    std::vector<H> sub_v(const std::vector<H> &a, const H &b)
+    {
+        std::vector<H> out;
+        if (!sched) {
+            for (const H &x : a) out.push_back(sub(x, b));
+            return out;
+        }
+        std::vector<Req> rs(a.size(), Req{R_SUB});
+        for (size_t i = 0; i < a.size(); i++) {
+            rs[i].a = a[i]->ct;
+            rs[i].b = b->ct;
+        }
+        return run_many(rs);
+    }
+    std::vector<H> mul_const_v(const std::vector<H> &a, double x)
+    {
+        std::vector<H> out;
+        if (!sched) {
+            for (const H &y : a) out.push_back(mul_const(y, x));
+            return out;
+        }
+        std::vector<Req> rs(a.size(), Req{R_MULC});
+        for (size_t i = 0; i < a.size(); i++) {
+            rs[i].a = a[i]->ct;
+            rs[i].x = x;
+        }
+        return run_many(rs);
+    }
+    // elementwise products a[i] * b[i] (b of size 1: broadcast)
+    std::vector<H> hmult_v(const std::vector<H> &a, const std::vector<H> &b)
+    {
+        auto rhs = [&](size_t i) { return b.size() == 1 ? b[0] : b[i]; };
+        std::vector<H> out;
+        if (a.size() == 1) {
+            out.push_back(hmult(a[0], rhs(0)));
+            return out;
+        }
+        if (!sched) {
+            std::vector<const CtObj *> as, bs;
+            for (size_t i = 0; i < a.size(); i++) {
+                as.push_back(a[i]->ct);
+                bs.push_back(rhs(i)->ct);
+            }
+            for (CtObj *p : hmult_grouped(c, k, as, bs)) out.push_back(w(p));
+            return out;
+        }
+        std::vector<Req> rs(a.size(), Req{R_HMULT});
+        for (size_t i = 0; i < a.size(); i++) {
+            rs[i].a = a[i]->ct;
+            rs[i].b = rhs(i)->ct;
+        }
+        return run_many(rs);
+    }
+    H sum(const std::vector<H> &x)
+    {
+        H acc = x[0];
+        for (size_t i = 1; i < x.size(); i++) acc = add(acc, x[i]);
+        return acc;
+    }
+
     // a level view: no GPU work, safe on any thread
     H drop(const H &a, int l) { return l == a->ct->level ? a : w(ev_drop(c, *a->ct, l)); }
     H rotsum(const H &a)
@@ -435,27 +565,17 @@ H col_sum(Ev &ev, const Col &x)
 H variance(Ev &ev, const Col &x, size_t n, double B, const H &R)
 {
     const double cst = 1.0 / (B * std::sqrt((double)n));
-    H acc;
-    for (const H &ct : x) {
-        H y = ev.mul_const(ct, cst);
-        H z = ev.hmult(y, y);
-        acc = acc ? ev.add(acc, z) : z;
-    }
-    H a = ev.rotsum(acc);
+    const Col y = ev.mul_const_v(x, cst);
+    H a = ev.rotsum(ev.sum(ev.hmult_v(y, y)));
     H m = ev.mul_const(R, 1.0 / (B * (double)n));
     return ev.sub(a, ev.hmult(m, m));
 }
 
 H centred_power_sum(Ev &ev, const Col &x, const H &mu, int power)
 {
-    H acc;
-    for (const H &ct : x) {
-        H x1 = ev.sub(ct, mu);
-        H x2 = ev.hmult(x1, x1);
-        H xp = power == 4 ? ev.hmult(x2, x2) : ev.hmult(x2, x1);
-        acc = acc ? ev.add(acc, xp) : xp;
-    }
-    return ev.rotsum(acc);
+    const Col x1 = ev.sub_v(x, mu);
+    const Col x2 = ev.hmult_v(x1, x1);
+    return ev.rotsum(ev.sum(ev.hmult_v(x2, power == 4 ? x2 : x1)));
 }
 
 Col znorm(Ev &ev, const Col &x, size_t n, double B, int k, int t)
@@ -463,9 +583,7 @@ Col znorm(Ev &ev, const Col &x, size_t n, double B, int k, int t)
     H R = ev.rotsum(col_sum(ev, x));
     H mu = ev.mul_const(R, 1.0 / (double)n);
     H inv = crypto_inv_sqrt(ev, variance(ev, x, n, B, R), B * B, k, t);
-    Col out;
-    for (const H &ct : x) out.push_back(ev.hmult(ev.sub(ct, mu), inv));
-    return out;
+    return ev.hmult_v(ev.sub_v(x, mu), Col{inv});
 }
 
 H kurt(Ev &ev, const Col &x, size_t n, double B, int k, int t)
@@ -516,12 +634,7 @@ H pcc(Ev &ev, const Col &x, const Col &y, size_t n, double Bx, double By, int k,
     H Ry = ev.rotsum(col_sum(ev, y));
     H mux = ev.mul_const(Rx, 1.0 / (double)n);
     H muy = ev.mul_const(Ry, 1.0 / (double)n);
-    H acc;
-    for (size_t i = 0; i < x.size(); i++) {
-        H p = ev.hmult(ev.sub(x[i], mux), ev.sub(y[i], muy));
-        acc = acc ? ev.add(acc, p) : p;
-    }
-    H Cs = ev.rotsum(acc);
+    H Cs = ev.rotsum(ev.sum(ev.hmult_v(ev.sub_v(x, mux), ev.sub_v(y, muy))));
     const int64_t pads = (int64_t)(x.size() * (size_t)ev.c.S) - (int64_t)n;
     if (pads) Cs = ev.sub(Cs, ev.mul_int(ev.hmult(mux, muy), pads));
     H cov = ev.mul_const(Cs, 1.0 / (double)n);
@@ -584,10 +697,10 @@ void run_queries(Ctx &c, const EvkObj &k, const std::vector<QueryIn> &qs, std::v
         return;
     }
     Sched sched{c, k};
-    sched.total = (int)qs.size();
     std::vector<ResObj *> res(qs.size(), nullptr);
     std::vector<std::exception_ptr> errs(qs.size());
     std::vector<std::thread> th;
+    for (size_t i = 0; i < qs.size(); i++) sched.worker_started();
     for (size_t i = 0; i < qs.size(); i++) {
         th.emplace_back([&, i] {
             try {
@@ -599,7 +712,7 @@ void run_queries(Ctx &c, const EvkObj &k, const std::vector<QueryIn> &qs, std::v
             sched.worker_finished();
         });
     }
-    sched.run();
+    sched.run(false);
     for (std::thread &t : th) t.join();
     for (size_t i = 0; i < qs.size(); i++) {
         if (errs[i]) {
@@ -610,4 +723,245 @@ void run_queries(Ctx &c, const EvkObj &k, const std::vector<QueryIn> &qs, std::v
     for (ResObj *r : res) out.push_back(r);
 }
 
+// ---------------------------------------------------------------------------
+// serving: continuous batching over the same scheduler
+// ---------------------------------------------------------------------------
+// A scheduler thread runs rounds forever; an admitted query gets a worker
+// thread that joins the next round (so requests that arrive while others run
+// are batched with them at op boundaries). Admission: at most max_batch
+// queries at once, and the sum of their working-set estimates within the HBM
+// budget. A query's estimate: (its ciphertexts + 40) full-size ciphertext
+// buffers (the deepest statistic keeps about 40 temporaries alive) plus one
+// item of key-switch workspace. Completion is marked when a CUDA event
+// recorded after the query's last op has completed (stream order).
+struct Server {
+    uint32_t tag = TAG_SRV;
+    Ctx *c;
+    const EvkObj *k;
+    size_t budget;
+    uint32_t max_batch;
+    Sched sched;
+    struct Ticket {
+        QueryIn q;
+        size_t est = 0;
+        std::chrono::steady_clock::time_point t_submit, t_ready;
+        ResObj *res = nullptr;
+        std::exception_ptr err;
+        cudaEvent_t ev = nullptr;
+        bool ready = false, taken = false;
+    };
+    std::mutex mu;
+    std::condition_variable cv_done, cv_compl, cv_idle;
+    std::map<uint64_t, std::shared_ptr<Ticket>> tickets;
+    std::deque<std::shared_ptr<Ticket>> queue, compl_q;
+    size_t reserved = 0;
+    uint32_t running = 0;
+    uint64_t next_id = 1;
+    bool stopping = false;
+    std::thread sched_thread, compl_thread;
+
+    Server(Ctx &cc, const EvkObj &kk, size_t b, uint32_t mb) : c(&cc), k(&kk), budget(b), max_batch(mb), sched{cc, kk}
+    {
+        sched_thread = std::thread([this] { sched.run(true); });
+        compl_thread = std::thread([this] { completion_loop(); });
+    }
+
+    size_t estimate(const QueryIn &q) const
+    {
+        const size_t ct_bytes = c->ct_words() * 8;
+        const size_t q1 = c->L + 1, e = c->ext_rows();
+        const size_t ws_item = (4 * q1 + (size_t)c->dnum * e + 2 * e + 2) * c->N * 8;
+        const size_t n = q.x->cts.size() + (q.y ? q.y->cts.size() : 0);
+        return (n + 40) * ct_bytes + ws_item;
+    }
+
+    // under mu
+    void try_admit()
+    {
+        while (!queue.empty() && running < max_batch && reserved + queue.front()->est <= budget) {
+            std::shared_ptr<Ticket> t = queue.front();
+            queue.pop_front();
+            reserved += t->est;
+            running++;
+            sched.worker_started();
+            std::thread([this, t] { work(t); }).detach();
+        }
+    }
+
+    void work(std::shared_ptr<Ticket> t)
+    {
+        try {
+            Ev ev{*c, *k, &sched};
+            t->res = run_one(ev, t->q);
+        } catch (...) {
+            t->err = std::current_exception();
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) cudaEventRecord(e, c->stream);
+        t->ev = e;
+        // leave the scheduler before `running` drops: the destructor tears the
+        // scheduler down as soon as no worker runs
+        sched.worker_finished();
+        std::lock_guard<std::mutex> lk(mu);
+        compl_q.push_back(t);
+        reserved -= t->est;
+        running--;
+        try_admit();
+        cv_compl.notify_one();
+        cv_idle.notify_all();
+    }
+
+    void completion_loop()
+    {
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            cv_compl.wait(lk, [&] { return !compl_q.empty() || (stopping && running == 0 && queue.empty()); });
+            if (compl_q.empty()) return;
+            std::shared_ptr<Ticket> t = compl_q.front();
+            compl_q.pop_front();
+            lk.unlock();
+            if (t->ev) {
+                cudaEventSynchronize(t->ev);
+                cudaEventDestroy(t->ev);
+                t->ev = nullptr;
+            }
+            lk.lock();
+            t->t_ready = std::chrono::steady_clock::now();
+            t->ready = true;
+            cv_done.notify_all();
+        }
+    }
+
+    uint64_t submit(const QueryIn &q)
+    {
+        auto t = std::make_shared<Ticket>();
+        t->q = q;
+        t->est = estimate(q);
+        if (t->est > budget) throw_err(PPST_E_BUDGET, "the query's working set exceeds the HBM budget");
+        std::lock_guard<std::mutex> lk(mu);
+        if (stopping) throw_err(PPST_E_STATE, "server is shutting down");
+        t->t_submit = std::chrono::steady_clock::now();
+        const uint64_t id = next_id++;
+        tickets[id] = t;
+        queue.push_back(t);
+        try_admit();
+        return id;
+    }
+
+    int wait(uint64_t id, int timeout_ms, ResObj **out)
+    {
+        std::unique_lock<std::mutex> lk(mu);
+        auto it = tickets.find(id);
+        if (it == tickets.end()) throw_err(PPST_E_ARG, "unknown ticket");
+        std::shared_ptr<Ticket> t = it->second;
+        if (t->taken) throw_err(PPST_E_STATE, "result already taken");
+        auto pred = [&] { return t->ready; };
+        if (timeout_ms < 0) cv_done.wait(lk, pred);
+        else if (!cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred)) return PPST_E_TIMEOUT;
+        t->taken = true;
+        if (t->err) std::rethrow_exception(t->err);
+        *out = t->res;
+        t->res = nullptr;
+        return PPST_OK;
+    }
+
+    double latency(uint64_t id)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = tickets.find(id);
+        if (it == tickets.end() || !it->second->ready) throw_err(PPST_E_STATE, "ticket not finished");
+        return std::chrono::duration<double>(it->second->t_ready - it->second->t_submit).count();
+    }
+
+    ~Server()
+    {
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            stopping = true;
+            cv_idle.wait(lk, [&] { return running == 0 && queue.empty(); });
+            cv_compl.notify_one();
+        }
+        sched.request_stop();
+        sched_thread.join();
+        compl_thread.join();
+        for (auto &kv : tickets)
+            if (kv.second->res) free_res(kv.second->res);
+        tag = TAG_DEAD;
+    }
+};
+
+void server_destroy(Server *s) { delete s; }
+
 }  // namespace ppst
+
+using namespace ppst;
+
+extern "C" {
+
+int ppst_server_create(ppst_ctx *ctx, const ppst_evk *evk, size_t hbm_budget, uint32_t max_batch, ppst_server **out)
+{
+    Ctx *c = (Ctx *)ctx;
+    const EvkObj *k = (const EvkObj *)evk;
+    if (!out) return PPST_E_ARG;
+    *out = nullptr;
+    if (!c || c->tag != TAG_CTX || !k || k->tag != TAG_EVK || k->ctx != c || max_batch < 1 || hbm_budget == 0)
+        return PPST_E_ARG;
+    try {
+        *out = (ppst_server *)new Server(*c, *k, hbm_budget, max_batch);
+        return PPST_OK;
+    } catch (...) {
+        return PPST_E_OOM;
+    }
+}
+
+int ppst_submit(ppst_server *srv, ppst_stat stat, const ppst_col *x, const ppst_col *y, const ppst_qopts *opts,
+                uint64_t *ticket)
+{
+    Server *s = (Server *)srv;
+    if (!s || s->tag != TAG_SRV || !ticket) return PPST_E_ARG;
+    try {
+        QueryIn q;
+        q.stat = stat;
+        q.x = (const ColObj *)x;
+        q.y = (const ColObj *)y;
+        q.o = opts ? *opts : ppst_qopts{1.0, 1.0, 7, 3};
+        validate_query(*s->c, q);
+        *ticket = s->submit(q);
+        return PPST_OK;
+    } catch (const PpstError &e) {
+        return s->c->fail(e.code, e.msg);
+    } catch (...) {
+        return PPST_E_ARG;
+    }
+}
+
+int ppst_wait(ppst_server *srv, uint64_t ticket, int32_t timeout_ms, ppst_res **out)
+{
+    Server *s = (Server *)srv;
+    if (!s || s->tag != TAG_SRV || !out) return PPST_E_ARG;
+    *out = nullptr;
+    try {
+        ResObj *r = nullptr;
+        const int rc = s->wait(ticket, timeout_ms, &r);
+        *out = (ppst_res *)r;
+        return rc;
+    } catch (const PpstError &e) {
+        return s->c->fail(e.code, e.msg);
+    } catch (...) {
+        return PPST_E_ARG;
+    }
+}
+
+int ppst_ticket_latency(ppst_server *srv, uint64_t ticket, double *seconds)
+{
+    Server *s = (Server *)srv;
+    if (!s || s->tag != TAG_SRV || !seconds) return PPST_E_ARG;
+    try {
+        *seconds = s->latency(ticket);
+        return PPST_OK;
+    } catch (const PpstError &e) {
+        return s->c->fail(e.code, e.msg);
+    }
+}
+
+}  // extern "C"
