@@ -105,7 +105,10 @@ int ppst_sync(ppst_ctx *ctx)
 {
     Ctx *c = (Ctx *)ctx;
     if (!ok(c, TAG_CTX)) return PPST_E_ARG;
-    return guard(c, [&] { PPST_CUDA(cudaStreamSynchronize(c->stream)); });
+    return guard(c, [&] {
+        PPST_CUDA(cudaStreamSynchronize(c->stream));
+        check_device_error(*c);
+    });
 }
 
 int ppst_mem_info(const ppst_ctx *ctx, size_t *in_use, size_t *cached)

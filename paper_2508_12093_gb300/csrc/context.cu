@@ -427,6 +427,15 @@ Ctx *ctx_create(const ppst_params &pin, const ppst_allocator *alloc, cudaStream_
                 twi[o] = Tw{ipw[r], h_shoup(ipw[r], qt)};
             }
         }
+        {
+            void *hp = nullptr;
+            PPST_CUDA(cudaHostAlloc(&hp, 64, cudaHostAllocMapped));
+            c->h_err = (volatile int *)hp;
+            *c->h_err = 0;
+            void *dp = nullptr;
+            PPST_CUDA(cudaHostGetDevicePointer(&dp, hp, 0));
+            c->d_err = (int *)dp;
+        }
         c->d_pc = upload(*c, c->hpc);
         c->d_twf = upload(*c, twf);
         c->d_twi = upload(*c, twi);
@@ -552,6 +561,12 @@ Ctx *ctx_create(const ppst_params &pin, const ppst_allocator *alloc, cudaStream_
                 md[b] = Tw{v, h_shoup(v, pm)};
             }
             c->d_md_outmul = upload(*c, md);
+            std::vector<Tw> mdt;
+            for (int l = 0; l <= L; l++) {
+                mdt.push_back(Tw{c->hpc[l].ninv, c->hpc[l].ninv_sh});
+                for (int m = 0; m < K; m++) mdt.push_back(md[m]);
+            }
+            c->d_md_outmul_top = upload(*c, mdt);
             c->md_const.assign((size_t)(L + 1) * (L + 1), MdC{});
             for (int l = 0; l <= L; l++) {
                 const uint64_t ql = c->primes[l];
@@ -586,15 +601,24 @@ void ctx_destroy(Ctx *c)
     c->pool.trim();
     // device tables and workspace are not in the free lists; release them directly
     std::vector<void *> own = {c->d_pc,          c->d_twf,      c->d_twi,   c->d_cdt,   c->d_ks,
-                               c->d_modup_outmul, c->d_md_outmul, c->d_md_const, c->ws_d2, c->ws_d2n,
+                               c->d_modup_outmul, c->d_md_outmul, c->d_md_outmul_top, c->d_md_const, c->ws_d2, c->ws_d2n,
                                c->ws_ext,         c->ws_acc,     c->ws_conv, c->ws_top};
     for (void *p : own) {
         if (!p) continue;
         if (c->pool.has_user) c->pool.user.release(c->pool.user.user, p, 0, (void *)c->stream);
         else cudaFree(p);
     }
+    if (c->h_err) cudaFreeHost((void *)c->h_err);
     c->tag = TAG_DEAD;
     delete c;
+}
+
+void check_device_error(Ctx &c)
+{
+    if (c.h_err && *c.h_err) {
+        *c.h_err = 0;
+        throw_err(PPST_E_CUDA, "a kernel's wait for its asynchronous copies timed out");
+    }
 }
 
 }  // namespace ppst

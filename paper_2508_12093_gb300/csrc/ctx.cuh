@@ -142,9 +142,14 @@ struct Ctx {
     Tw *d_modup_outmul = nullptr;
     std::vector<size_t> modup_outmul_off;
     Tw *d_md_outmul = nullptr;
+    Tw *d_md_outmul_top = nullptr;  // per level l: N^-1 mod q_l, then the K entries of d_md_outmul
     MdC *d_md_const = nullptr;
     std::vector<MdC> md_const;
     cudaStream_t stream = nullptr;
+    // error word that kernels with bounded waits set on a timeout: pinned,
+    // mapped host memory, readable without synchronising the stream
+    volatile int *h_err = nullptr;
+    int *d_err = nullptr;
     Pool pool;
     Error err{0, ""};
     std::mutex err_mu;  // server threads may record errors concurrently
@@ -304,6 +309,9 @@ struct QueryIn {
 };
 void run_queries(Ctx &c, const EvkObj &k, const std::vector<QueryIn> &qs, std::vector<ResObj *> &out);
 void validate_query(const Ctx &c, const QueryIn &q);  // PPST_E_ARG on a malformed query
+// PPST_E_CUDA if a kernel reported a timed-out wait (the word is then cleared);
+// call once the work in question has completed
+void check_device_error(Ctx &c);
 
 // ---- serving (stats.cu) ----
 struct Server;

@@ -308,6 +308,7 @@ void decrypt_to_slots(Ctx &c, const SkObj &sk, const CtObj &ct, std::vector<doub
     std::vector<uint64_t> h((size_t)nl * N);
     PPST_CUDA(cudaMemcpyAsync(h.data(), mr.p, h.size() * 8, cudaMemcpyDeviceToHost, c.stream));
     PPST_CUDA(cudaStreamSynchronize(c.stream));
+    check_device_error(c);
     Crt crt(std::vector<uint64_t>(c.primes.begin(), c.primes.begin() + nl));
     std::vector<std::complex<double>> v(N);
     for (int i = 0; i < N; i++) {
@@ -338,6 +339,7 @@ void export_ct(Ctx &c, const CtObj &ct, uint64_t *c0, uint64_t *c1)
     PPST_CUDA(cudaMemcpyAsync(c0, t.p, (size_t)nl * N * 8, cudaMemcpyDeviceToHost, c.stream));
     PPST_CUDA(cudaMemcpyAsync(c1, t.u64() + ps, (size_t)nl * N * 8, cudaMemcpyDeviceToHost, c.stream));
     PPST_CUDA(cudaStreamSynchronize(c.stream));
+    check_device_error(c);
 }
 
 CtObj *import_ct(Ctx &c, const uint64_t *c0, const uint64_t *c1, int level, double scale)

@@ -27,6 +27,9 @@
 // through each stage in one launch. The item is the fastest-varying block
 // index of the inner-product kernel, so the blocks that read the same key
 // tile run back to back and the tile is fetched from HBM once per batch.
+#include <atomic>
+
+#include "bulk.cuh"
 #include "ntt.cuh"
 
 namespace ppst {
@@ -185,54 +188,108 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
 // ---------------------------------------------------------------------------
 // 3. CHUNKS pass fused with the key inner product
 // ---------------------------------------------------------------------------
+// A block owns SUB consecutive chunks (one contiguous tile of SUB M words) of
+// target limb e and loops over the digits. The digit tiles and the two key
+// tiles of a digit are brought into shared memory by bulk asynchronous copies:
+// digit j + 2 and the keys of digit j + 1 are in flight while digit j is
+// transformed and accumulated, so the HBM latency is off the critical path.
+template <int S>
+struct InnerSmem {
+    typedef PassShape<S> P;
+    static constexpr int TILE = P::SUB * P::M;  // words per tile
+    static constexpr size_t X_OFF = 128;        // after the barriers: two digit tiles
+    static constexpr size_t K_OFF = X_OFF + 2 * (size_t)TILE * 8;  // two key tiles
+    static constexpr size_t T_OFF = K_OFF + 2 * (size_t)TILE * 8;  // transpose buffer
+    static constexpr size_t BYTES = T_OFF + (size_t)P::SMEM_WORDS * 8;
+};
+
 template <int S>
 __global__ void __launch_bounds__(PassShape<S>::THREADS, 1)
     k_inner_chunks(const uint64_t *__restrict__ ext, const uint64_t *__restrict__ d2n, const uint64_t *__restrict__ key,
                    uint64_t *__restrict__ acc, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN,
-                   int level, int alpha, int L, int K, int nd, size_t ext_stride, int B, Ws ws)
+                   int level, int alpha, int L, int K, int nd, size_t ext_stride, int B, Ws ws, int *err)
 {
     typedef PassShape<S> P;
-    __shared__ uint64_t sm[P::SMEM_WORDS];
+    typedef InnerSmem<S> SM;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);  // [0], [1]: digit stages; [2]: key stage
+    uint64_t *xs = reinterpret_cast<uint64_t *>(smem + SM::X_OFF);
+    uint64_t *ks = reinterpret_cast<uint64_t *>(smem + SM::K_OFF);
+    uint64_t *sm = reinterpret_cast<uint64_t *>(smem + SM::T_OFF);
+    constexpr uint32_t TB = SM::TILE * 8;
     const int N = 1 << logN;
     const int it = blockIdx.x % B, tile = blockIdx.x / B;
     const int e = blockIdx.y;
     const int row = e <= level ? e : L + 1 + (e - level - 1);
     const PrimeC p = pc[row];
     const Tw *T = tw + (size_t)row * N;
+    const size_t krow = (size_t)(L + 1 + K) * N;
+    const size_t t0 = (size_t)tile * SM::TILE;
+    const uint64_t *exte = ext + it * ws.ext + (size_t)e * N + t0;
+    const uint64_t *d2ne = d2n + it * ws.d2 + (size_t)e * N + t0;
+    const uint64_t *keye = key + (size_t)row * N + t0;
+    // a digit's own limbs come from d in the evaluation domain (block-uniform)
+    auto own = [&](int j) { return e >= j * alpha && e < min(j * alpha + alpha, level + 1); };
+    auto load_digit = [&](int j) {
+        mbar_arrive_expect_tx(&bar[j & 1], TB);
+        bulk_g2s(xs + (j & 1) * SM::TILE, own(j) ? d2ne : exte + (size_t)j * ext_stride, TB, &bar[j & 1]);
+    };
+    auto load_keys = [&](int j) {
+        mbar_arrive_expect_tx(&bar[2], 2 * TB);
+        bulk_g2s(ks, keye + (size_t)j * 2 * krow, TB, &bar[2]);
+        bulk_g2s(ks + SM::TILE, keye + (size_t)j * 2 * krow + krow, TB, &bar[2]);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init(&bar[2], 1);
+        mbar_fence_init();
+        load_digit(0);
+        if (nd > 1) load_digit(1);
+        load_keys(0);
+    }
+    __syncthreads();
     int h, sub;
     pass_coords<S, false>(h, sub);
     const int g = tile * P::SUB + sub;
-    const size_t krow = (size_t)(L + 1 + K) * N;
-    // this thread's words (natural E h + k) are stored at fin + T k
-    const size_t fin = (size_t)g * P::M + h;
-    const uint64_t *exti = ext + it * ws.ext, *d2ni = d2n + it * ws.d2;
+    const int w0 = sub * P::M + h;  // this thread's words of a tile: w0 + T k
     uint64_t a0[P::E], a1[P::E];
 #pragma unroll
     for (int k = 0; k < P::E; k++) a0[k] = a1[k] = 0;
-    for (int j = 0; j < nd; j++) {
-        const int lo = j * alpha, hi = min(lo + alpha, level + 1);
+    int j = 0;
+    for (; j < nd; j++) {
+        if (__syncthreads_or(!mbar_wait(&bar[j & 1], (j >> 1) & 1))) break;
         uint64_t x[P::E];
-        if (e >= lo && e < hi) {  // block-uniform
-            const uint64_t *src = d2ni + (size_t)e * N + fin;
+        const uint64_t *xt = xs + (j & 1) * SM::TILE + w0;
 #pragma unroll
-            for (int k = 0; k < P::E; k++) x[k] = src[P::T * k];
-        } else {
-            const uint64_t *src = exti + (size_t)j * ext_stride + (size_t)e * N + (size_t)g * P::M;
-#pragma unroll
-            for (int k = 0; k < P::E; k++) x[k] = src[h + P::T * k];
+        for (int k = 0; k < P::E; k++) x[k] = xt[P::T * k];
+        if (!own(j)) {
             chunks_fwd_core<S>(x, sm, h, sub, g, N, T, p.q);
 #pragma unroll
             for (int k = 0; k < P::E; k++) x[k] = reduce4q(x[k], p.q);
         }
-        const uint64_t *k0 = key + (size_t)j * 2 * krow + (size_t)row * N + fin;
-        const uint64_t *k1 = k0 + krow;
+        if (__syncthreads_or(!mbar_wait(&bar[2], j & 1))) break;
+        const uint64_t *k0 = ks + w0, *k1 = k0 + SM::TILE;
 #pragma unroll
         for (int k = 0; k < P::E; k++) {
             a0[k] = add_mod(a0[k], mont_mul(x[k], k0[P::T * k], p.q, p.qinv), p.q);
             a1[k] = add_mod(a1[k], mont_mul(x[k], k1[P::T * k], p.q, p.qinv), p.q);
         }
+        __syncthreads();  // digit stage j & 1 and the key stage are free again
+        if (threadIdx.x == 0) {
+            if (j + 2 < nd) load_digit(j + 2);
+            if (j + 1 < nd) load_keys(j + 1);
+        }
     }
-    uint64_t *o0 = acc + it * ws.acc + (size_t)e * N + fin, *o1 = o0 + krow;
+    if (j < nd) {  // a copy did not arrive in time: report, drain what is in flight, give up
+        if (threadIdx.x == 0) {
+            *(volatile int *)err = 1;
+            for (int d = j; d < min(j + 2, nd); d++) mbar_wait(&bar[d & 1], (d >> 1) & 1);
+            mbar_wait(&bar[2], j & 1);
+        }
+        return;
+    }
+    uint64_t *o0 = acc + it * ws.acc + (size_t)e * N + t0 + w0, *o1 = o0 + krow;
 #pragma unroll
     for (int k = 0; k < P::E; k++) {
         o0[P::T * k] = a0[k];
@@ -244,20 +301,21 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 1)
 // ModDown (+ rescale)
 // ---------------------------------------------------------------------------
 // u_k = d_k[l] + acc_k[l] P^-1 (evaluation domain), the top limb before its inverse transform
-__global__ void k_md_top_kernel(ItemPtrs ip, const uint64_t *__restrict__ acc, uint64_t *__restrict__ top,
-                                const PrimeC *__restrict__ pc, Tw pinv, int N, int level, size_t pstride,
-                                size_t ext_stride, Ws ws)
+__global__ void k_md_top_kernel(ItemPtrs ip, uint64_t *__restrict__ acc, const PrimeC *__restrict__ pc, Tw pinv,
+                                int N, int level, size_t pstride, size_t ext_stride, Ws ws)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     const int it = blockIdx.y / 2, k = blockIdx.y - 2 * it;
     const uint64_t q = pc[level].q;
     const size_t o = (size_t)level * N + c;
-    const uint64_t v = csub(shoup(acc[it * ws.acc + (size_t)k * ext_stride + o], pinv.w, pinv.s, q), q);
-    top[it * ws.top + (size_t)k * N + c] = add_mod(ip.in0[it][(size_t)k * pstride + o], v, q);
+    uint64_t *a = acc + it * ws.acc + (size_t)k * ext_stride + o;
+    const uint64_t v = csub(shoup(*a, pinv.w, pinv.s, q), q);
+    *a = add_mod(ip.in0[it][(size_t)k * pstride + o], v, q);  // in place: row l of acc_k is not needed otherwise
 }
 
-// top_k -= conv_l(y_k) P^-1 (coefficient domain), y_k = P rows of acc_k after ModDown's first factor
+// top_k = INTT(u_k) - conv_l(y_k) P^-1 (coefficient domain): INTT(u_k) is row l of acc_k, y_k its P rows
+// after ModDown's first factor
 __global__ void k_md_topfix_kernel(const uint64_t *__restrict__ acc, uint64_t *__restrict__ top,
                                    const uint64_t *__restrict__ hMP, const PrimeC *__restrict__ pc, Tw pinv, int N,
                                    int level, int L, int K, size_t ext_stride, Ws ws)
@@ -271,8 +329,8 @@ __global__ void k_md_topfix_kernel(const uint64_t *__restrict__ acc, uint64_t *_
     for (int m = 0; m < K; m++) mac(a, ym[(size_t)m * N], hMP[(size_t)m * (L + 1) + level]);
     const uint64_t conv = mont_redc(a.hi, a.lo, p.q, p.qinv);
     const uint64_t v = csub(shoup(conv, pinv.w, pinv.s, p.q), p.q);
-    uint64_t *tp = top + it * ws.top + (size_t)k * N + c;
-    *tp = sub_mod(*tp, v, p.q);
+    const uint64_t u = acc[it * ws.acc + (size_t)k * ext_stride + (size_t)level * N + c];
+    top[it * ws.top + (size_t)k * N + c] = sub_mod(u, v, p.q);
 }
 
 // COLS pass of z_i = conv_i(y) P^-1 (+ [top]_centred mod q_i when rescaling), limbs i < nl of both polys
@@ -402,9 +460,16 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
     ProfScope _ps(c, "inner_chunks", (uint64_t)B * E_ext * (3 * nd + 2));
     dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
-        const dim3 grid(B * ((c.N >> S) / 16), E_ext);
-        k_inner_chunks<S><<<grid, PassShape<S>::THREADS, 0, c.stream>>>(
-            c.ws_ext, c.ws_d2n, key.d, c.ws_acc, c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, B, ws);
+        const dim3 grid(B * ((c.N >> S) / PassShape<S>::SUB), E_ext);
+        const size_t smem = InnerSmem<S>::BYTES;
+        static std::atomic<bool> attr_set{false};
+        if (!attr_set.load()) {
+            PPST_CUDA(cudaFuncSetAttribute(k_inner_chunks<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr_set = true;
+        }
+        k_inner_chunks<S><<<grid, PassShape<S>::THREADS, smem, c.stream>>>(
+            c.ws_ext, c.ws_d2n, key.d, c.ws_acc, c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, B, ws,
+            c.d_err);
     });
     check_launch("k_inner_chunks");
 }
@@ -423,16 +488,20 @@ static void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip)
     const dim3 eg(c.N / 256, 2 * B);
     if (RESC) {
         ProfScope _ps(c, "moddown_top", (uint64_t)6 * B);
-        k_md_top_kernel<<<eg, 256, 0, c.stream>>>(ip, c.ws_acc, c.ws_top, c.d_pc, hm.pinv, c.N, level, ps, es, ws);
+        k_md_top_kernel<<<eg, 256, 0, c.stream>>>(ip, c.ws_acc, c.d_pc, hm.pinv, c.N, level, ps, es, ws);
         check_launch("k_md_top");
+        // rows l .. l + K of both accumulators of every item (the top limb u_k, then
+        // the P rows) to the coefficient domain in one transform: row l times N^-1,
+        // P row m times N^-1 (P / p_m)^-1
+        LimbMap mp{c.ws_acc + (size_t)level * c.N, es, c.K + 1, 2 * B, 1, level, c.L + 1};
+        ntt_inv_mul(c, mp, c.d_md_outmul_top + (size_t)level * (c.K + 1));
+    } else {
+        // P rows of both accumulators of every item to the coefficient domain, times (P / p_m)^-1
+        LimbMap mp{c.ws_acc + (size_t)(level + 1) * c.N, es, c.K, 2 * B, 0, 0, c.L + 1};
+        ntt_inv_mul(c, mp, c.d_md_outmul);
     }
-    // P rows of both accumulators of every item to the coefficient domain, times (P / p_m)^-1
-    LimbMap mp{c.ws_acc + (size_t)(level + 1) * c.N, es, c.K, 2 * B, 0, 0, c.L + 1};
-    ntt_inv_mul(c, mp, c.d_md_outmul);
     const uint64_t *hMP = c.d_ks + c.moddown_off + 2 * c.K;
     if (RESC) {
-        LimbMap mt{c.ws_top, (size_t)c.N, 1, 2 * B, 1, level, 0};
-        ntt_inv(c, mt);
         ProfScope _ps(c, "moddown_top", (uint64_t)B * (2 * c.K + 4));
         k_md_topfix_kernel<<<eg, 256, 0, c.stream>>>(c.ws_acc, c.ws_top, hMP, c.d_pc, hm.pinv, c.N, level, c.L, c.K,
                                                       es, ws);

@@ -825,6 +825,13 @@ struct Server {
                 cudaEventDestroy(t->ev);
                 t->ev = nullptr;
             }
+            if (!t->err) {
+                try {
+                    check_device_error(*c);
+                } catch (...) {
+                    t->err = std::current_exception();
+                }
+            }
             lk.lock();
             t->t_ready = std::chrono::steady_clock::now();
             t->ready = true;
