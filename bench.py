@@ -220,6 +220,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--served", type=int, default=64, help="queries in the served-stream sample (0: skip)")
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the 64-column batched workload and the dnum autotuner")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     if args.impl == "reference":
@@ -311,13 +313,9 @@ def main():
     clk = clocks.stop()
     launches = ctx.launch_count() - l0
     t_ms = e_start.elapsed_time(e_end)
-    if dist:
-        t = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms = replica_max(t_ms, dist)
     n_dom, ms_dom, units_dom = ctx.prof_read(dom, with_units=True)
-    queries = len(STATS) * args.steps * world
-    value = queries / (t_ms / 1000.0)
+    value = whole_job_rate(len(STATS) * args.steps, world, t_ms / 1000.0)
 
     # the plain form: the same queries one at a time
     for _ in range(2):
@@ -333,6 +331,8 @@ def main():
     lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
 
     srv = served_stream(pp, ctx, sk, evk, ost, args.served) if args.served > 0 else None
+    peak, peak_kind = peaks()
+    b64 = batched64(pp, ost, PARAMS, peak) if args.batched else None
 
     # roofline of the dominant kernel: algorithmic bytes = the limbs it must
     # read once plus the limbs it writes (the library counts them per launch)
@@ -384,11 +384,8 @@ def main():
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = len(STATS) * e2e_steps * world / e2e_s
+    e2e_s = replica_max(e2e_s, dist)
+    e2e_value = whole_job_rate(len(STATS) * e2e_steps, world, e2e_s)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -413,6 +410,11 @@ def main():
                             "mode": "served stream (below)"} if srv else
                            {"p50": pct(lat_ms, 50), "p99": pct(lat_ms, 99), "mode": "one query at a time"}),
             "served": srv,
+            "batched64": b64,
+            "hmult_ks_by_dnum": ({str(r["dnum"]): {"us": r["hmult_us"], "algorithmic_bytes": r["algorithmic_bytes"],
+                                                   "frac_of_hbm": r.get("hmult_frac_of_hbm"),
+                                                   "rotate_us": r["rotate_us"], "skew_query_ms": r["query_us"] / 1e3}
+                                  for r in b64["autotune"]} if b64 else None),
             "hmult_ks": {"us": hmult_us, "algorithmic_bytes": HMULT_BYTES, "achieved_gbs": hmult_gbs,
                          "frac_of_hbm": hmult_gbs / peak},
             "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -431,6 +433,23 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def replica_max(x, dist):
+    """The maximum of x over all ranks (replicas time the same work; the job
+    takes as long as the slowest)."""
+    if not dist:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units processed by all replicas per second of the slowest one."""
+    return units_per_rank * world / seconds
 
 
 def pct(xs, p):
@@ -519,6 +538,86 @@ def served_stream(pp, ctx, sk, evk, ost, count):
                        f"Pearson uniformly over {SERVED_COLS} lognormal columns and {SERVED_PAIRS} Bernoulli/"
                        f"lognormal pairs of log-uniform 1k-1M rows (N=2^16, multi-ciphertext), keys and "
                        f"columns resident; arrivals at 3x the one-at-a-time capacity")}
+
+
+BATCH_COLS = 64  # columns of the batched workload (pairs 2i, 2i + 1 for Pearson correlation)
+
+
+def batched_columns(pp_ctx, evk, seed=700):
+    """64 columns of log-uniform 1k-32k rows in 32 pairs: a Bernoulli(0.2)
+    column b and y = (lognormal(9, 0.6) + 20000 b + N(0, 3000^2)) / 1000."""
+    import numpy as np
+    lens = workloads.log_uniform_lengths(BATCH_COLS // 2, 1024, 32768, seed=seed)
+    cols, data = [], []
+    for i in range(0, BATCH_COLS, 2):
+        b, y = workloads.pcc_pair(int(lens[i // 2]), seed=seed + 1 + i)
+        for j, x in enumerate((y, b)):
+            cols.append(pp_ctx.encrypt_column(evk, x, seed + 100 + i + j))
+            data.append(x)
+    return cols, data
+
+
+def batched_queries(cols):
+    """All five statistics: Z-score, CV, skewness, kurtosis of every column, Pearson
+    correlation of every pair; B = 20 for lognormal columns, 1 for Bernoulli."""
+    qs = []
+    for i, c in enumerate(cols):
+        B = 20.0 if i % 2 == 0 else 1.0
+        for st in ("zscore", "cv", "skew", "kurt"):
+            qs.append((st, c, None, dict(B_x=B, cheb_log2deg=7, newton_steps=3), (i,)))
+    for i in range(0, len(cols), 2):
+        qs.append(("pcc", cols[i], cols[i + 1], dict(B_x=20.0, B_y=1.0, cheb_log2deg=7, newton_steps=3), (i, i + 1)))
+    return qs
+
+
+def batched64(pp, ost, params, peak):
+    """The batched workload on the autotuned dnum: every query queued at once
+    into the request loop (continuous batching, up to 32 in flight), against
+    the same queries one at a time."""
+    import numpy as np
+    import torch
+    from paper_2508_12093_gb300 import autotune
+    best, table = autotune.tune(params, cache=None, peak_gbs=peak)
+    prm = autotune.with_dnum(params, best)
+    ctx = pp.Context(prm)
+    sk, evk = ctx.keygen(2)
+    cols, data = batched_columns(ctx, evk)
+    qs = batched_queries(cols)
+    for q in qs[:4]:  # warm-up
+        ctx.query(evk, *q[:4])
+    ctx.sync()
+    t0 = time.perf_counter()
+    for q in qs:
+        ctx.query(evk, *q[:4])
+    ctx.sync()
+    serial_s = time.perf_counter() - t0
+    srv = pp.Server(ctx, evk, SERVED_BUDGET, 32)
+    l0 = ctx.launch_count()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ts = [srv.submit(*q[:4]) for q in qs]
+    res = [srv.wait(t) for t in ts]
+    batch_s = time.perf_counter() - t0
+    launches = ctx.launch_count() - l0
+    srv.close()
+    worst = 0.0
+    for q, r in zip(qs, res):
+        vals, _ = ctx.decrypt(sk, r)
+        if q[0] == "pcc":
+            want = np.array([ost.plain_stats(data[q[4][0]], data[q[4][1]])["pcc"]])
+        else:
+            ref = ost.plain_stats(data[q[4][0]])
+            want = ref["znorm"] if q[0] == "zscore" else np.array([ref[q[0]]])
+        worst = max(worst, float(np.abs(vals[:len(want)] - want).max() / np.abs(want).max()))
+    ctx.close()
+    return {"value": len(qs) / batch_s, "unit": "queries/s", "serial_value": len(qs) / serial_s,
+            "speedup_vs_serial": serial_s / batch_s, "queries": len(qs), "dnum": best, "gpu_launches": launches,
+            "max_rel_err_vs_fp64": worst,
+            "workload": (f"{BATCH_COLS} columns of log-uniform 1k-32k rows (one ciphertext each), in pairs of "
+                         "y = (lognormal(9, 0.6) + 20000 b + N(0, 3000^2))/1000 and b ~ Bernoulli(0.2); Z-score, CV, skewness, kurtosis of every "
+                         "column and Pearson correlation of every pair (B=20 lognormal, 1 Bernoulli), "
+                         "Chebyshev degree 127, 3 Newton steps, dnum autotuned over {3,4,6,12}"),
+            "autotune": table}
 
 
 def ctx_scale(ctx):

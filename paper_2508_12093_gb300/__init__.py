@@ -11,6 +11,7 @@ its caching allocator) and the CUDA stream; numpy arrays carry host buffers.
     values, report = ctx.decrypt(sk, res)
 """
 import ctypes
+import weakref
 
 import numpy as np
 
@@ -35,6 +36,9 @@ def _u64(a):
 class _Handle:
     def __init__(self, ctx, ptr):
         self.ctx, self.ptr = ctx, ptr
+        live = getattr(ctx, "_live", None)
+        if live is not None:
+            live.add(self)  # closing the context frees the handle first
 
     def close(self):
         if self.ptr:
@@ -162,6 +166,7 @@ class Context:
 
     def __init__(self, params, use_torch=True, stream=None):
         self.params = dict(params)
+        self._live = weakref.WeakSet()
         prm = ppst_params(params["log_n"], params["n_q"], params["n_p"], params["dnum"], params["q0_bits"],
                           params["q_bits"], params["p_bits"], float(params["log_scale"]),
                           float(params.get("sigma", 0.0)), int(params.get("gauss_bound", 0)))
@@ -200,7 +205,15 @@ class Context:
         self.K = params["n_p"]
 
     def close(self):
+        """Frees every live handle of this context (servers first: they drain
+        their queries), then the context itself."""
         if getattr(self, "ptr", None):
+            live = list(getattr(self, "_live", ()))
+            for h in live:
+                if isinstance(h, Server):
+                    h.close()
+            for h in live:
+                h.close()
             lib.ppst_free(self.ptr)
             self.ptr = None
 

@@ -27,6 +27,7 @@
 #include <memory>
 #include <mutex>
 #include <thread>
+#include <tuple>
 
 #include "ctx.cuh"
 
@@ -159,6 +160,47 @@ struct Sched {
         cv_sched.notify_one();
     }
 
+    // ---- values shared by the queries in flight: a column's rotate-and-sum
+    // and its variance for a given B are computed by the first query that needs
+    // them and reused by the others (the same ops on the same inputs: results
+    // are bit-identical to a query run alone) ----
+    struct Shared {
+        bool ready = false;
+        H val;
+        std::exception_ptr err;
+    };
+    typedef std::tuple<const void *, int, double> SKey;
+    std::map<SKey, std::shared_ptr<Shared>> shared;
+    std::map<const void *, int> col_users;  // queries in flight per column
+    std::condition_variable cv_shared;
+
+    void col_acquire(const void *col)
+    {
+        if (!col) return;
+        std::lock_guard<std::mutex> lk(mu);
+        col_users[col]++;
+    }
+
+    // the last query on a column drops the column's shared values
+    void col_release(const void *col)
+    {
+        if (!col) return;
+        std::vector<H> drop;  // freed outside the lock
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            if (--col_users[col] > 0) return;
+            col_users.erase(col);
+            for (auto it = shared.begin(); it != shared.end();) {
+                if (std::get<0>(it->first) == col) {
+                    drop.push_back(it->second->val);
+                    it = shared.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        }
+    }
+
     void exec_one(Req &r)
     {
         switch (r.kind) {
@@ -261,7 +303,9 @@ struct Sched {
     {
         std::unique_lock<std::mutex> lk(mu);
         for (;;) {
-            cv_sched.wait(lk, [&] { return (active > 0 && waiting == active) || (active == 0 && (!forever || stop)); });
+            cv_sched.wait(lk, [&] {
+                return (active > 0 && waiting == active && !pending.empty()) || (active == 0 && (!forever || stop));
+            });
             if (active == 0) return;
             std::vector<Req *> batch;
             batch.swap(pending);
@@ -418,6 +462,58 @@ struct Ev {
         return acc;
     }
 
+    // a value shared with the other queries in flight (see Sched::Shared); a
+    // query that finds it being computed waits without holding up the rounds
+    template <class F>
+    H shared_value(const void *col, int kind, double b, F &&compute)
+    {
+        if (!sched || !col) return compute();
+        const Sched::SKey key{col, kind, b};
+        std::shared_ptr<Sched::Shared> e;
+        bool mine = false;
+        {
+            std::lock_guard<std::mutex> lk(sched->mu);
+            std::shared_ptr<Sched::Shared> &slot = sched->shared[key];
+            if (!slot) {
+                slot = std::make_shared<Sched::Shared>();
+                mine = true;
+            }
+            e = slot;
+        }
+        if (mine) {
+            try {
+                H v = compute();
+                {
+                    std::lock_guard<std::mutex> lk(sched->mu);
+                    e->val = v;
+                    e->ready = true;
+                }
+                sched->cv_shared.notify_all();
+                return v;
+            } catch (...) {
+                {
+                    std::lock_guard<std::mutex> lk(sched->mu);
+                    e->err = std::current_exception();
+                    e->ready = true;
+                    sched->shared.erase(key);  // a later query computes it afresh
+                }
+                sched->cv_shared.notify_all();
+                throw;
+            }
+        }
+        {
+            std::unique_lock<std::mutex> lk(sched->mu);
+            if (!e->ready) {
+                sched->waiting++;  // parked: the rounds go on without this worker
+                sched->cv_sched.notify_one();
+                sched->cv_shared.wait(lk, [&] { return e->ready; });
+                sched->waiting--;
+            }
+        }
+        if (e->err) std::rethrow_exception(e->err);
+        return e->val;
+    }
+
     // a level view: no GPU work, safe on any thread
     H drop(const H &a, int l) { return l == a->ct->level ? a : w(ev_drop(c, *a->ct, l)); }
     H rotsum(const H &a)
@@ -571,6 +667,18 @@ H variance(Ev &ev, const Col &x, size_t n, double B, const H &R)
     return ev.sub(a, ev.hmult(m, m));
 }
 
+// rotsum of the column's entries: Mean's sum (Sec. 6.1), shared per column
+H col_rsum(Ev &ev, const Col &x, const void *kx)
+{
+    return ev.shared_value(kx, 0, 0.0, [&] { return ev.rotsum(col_sum(ev, x)); });
+}
+
+// Variance(x, B) (Eq. 2), shared per column and B
+H col_var(Ev &ev, const Col &x, size_t n, double B, const H &R, const void *kx)
+{
+    return ev.shared_value(kx, 1, B, [&] { return variance(ev, x, n, B, R); });
+}
+
 H centred_power_sum(Ev &ev, const Col &x, const H &mu, int power)
 {
     const Col x1 = ev.sub_v(x, mu);
@@ -578,17 +686,17 @@ H centred_power_sum(Ev &ev, const Col &x, const H &mu, int power)
     return ev.rotsum(ev.sum(ev.hmult_v(x2, power == 4 ? x2 : x1)));
 }
 
-Col znorm(Ev &ev, const Col &x, size_t n, double B, int k, int t)
+Col znorm(Ev &ev, const Col &x, size_t n, double B, int k, int t, const void *kx)
 {
-    H R = ev.rotsum(col_sum(ev, x));
+    H R = col_rsum(ev, x, kx);
     H mu = ev.mul_const(R, 1.0 / (double)n);
-    H inv = crypto_inv_sqrt(ev, variance(ev, x, n, B, R), B * B, k, t);
+    H inv = crypto_inv_sqrt(ev, col_var(ev, x, n, B, R, kx), B * B, k, t);
     return ev.hmult_v(ev.sub_v(x, mu), Col{inv});
 }
 
-H kurt(Ev &ev, const Col &x, size_t n, double B, int k, int t)
+H kurt(Ev &ev, const Col &x, size_t n, double B, int k, int t, const void *kx)
 {
-    H R = ev.rotsum(col_sum(ev, x));
+    H R = col_rsum(ev, x, kx);
     H mu = ev.mul_const(R, 1.0 / (double)n);
     H X = centred_power_sum(ev, x, mu, 4);
     const int64_t pads = (int64_t)(x.size() * (size_t)ev.c.S) - (int64_t)n;
@@ -597,14 +705,14 @@ H kurt(Ev &ev, const Col &x, size_t n, double B, int k, int t)
         X = ev.sub(X, ev.mul_int(ev.hmult(mu2, mu2), pads));
     }
     H num = ev.mul_const(X, 1.0 / (double)n);
-    H inv = crypto_inv_sqrt(ev, variance(ev, x, n, B, R), B * B, k, t);
+    H inv = crypto_inv_sqrt(ev, col_var(ev, x, n, B, R, kx), B * B, k, t);
     H inv2 = ev.hmult(inv, inv);
     return ev.hmult(num, ev.hmult(inv2, inv2));
 }
 
-H skew(Ev &ev, const Col &x, size_t n, double B, int k, int t)
+H skew(Ev &ev, const Col &x, size_t n, double B, int k, int t, const void *kx)
 {
-    H R = ev.rotsum(col_sum(ev, x));
+    H R = col_rsum(ev, x, kx);
     H mu = ev.mul_const(R, 1.0 / (double)n);
     H X = centred_power_sum(ev, x, mu, 3);
     const int64_t pads = (int64_t)(x.size() * (size_t)ev.c.S) - (int64_t)n;
@@ -613,33 +721,34 @@ H skew(Ev &ev, const Col &x, size_t n, double B, int k, int t)
         X = ev.add(X, ev.mul_int(ev.hmult(mu2, mu), pads));
     }
     H num = ev.mul_const(X, 1.0 / (double)n);
-    H inv = crypto_inv_sqrt(ev, variance(ev, x, n, B, R), B * B, k, t);
+    H inv = crypto_inv_sqrt(ev, col_var(ev, x, n, B, R, kx), B * B, k, t);
     H inv3 = ev.hmult(ev.hmult(inv, inv), inv);
     return ev.hmult(num, inv3);
 }
 
-H cv(Ev &ev, const Col &x, size_t n, double B, int k, int t)
+H cv(Ev &ev, const Col &x, size_t n, double B, int k, int t, const void *kx)
 {
-    H R = ev.rotsum(col_sum(ev, x));
+    H R = col_rsum(ev, x, kx);
     H muB = ev.mul_const(R, 1.0 / (B * (double)n));
     H isq = crypto_inv_sqrt(ev, muB, B, k, t);
     H mu_inv = ev.hmult(isq, isq);
-    H std_ = crypto_sqrt(ev, variance(ev, x, n, B, R), B * B, k);
+    H std_ = crypto_sqrt(ev, col_var(ev, x, n, B, R, kx), B * B, k);
     return ev.hmult(std_, mu_inv);
 }
 
-H pcc(Ev &ev, const Col &x, const Col &y, size_t n, double Bx, double By, int k, int t)
+H pcc(Ev &ev, const Col &x, const Col &y, size_t n, double Bx, double By, int k, int t, const void *kx,
+      const void *ky)
 {
-    H Rx = ev.rotsum(col_sum(ev, x));
-    H Ry = ev.rotsum(col_sum(ev, y));
+    H Rx = col_rsum(ev, x, kx);
+    H Ry = col_rsum(ev, y, ky);
     H mux = ev.mul_const(Rx, 1.0 / (double)n);
     H muy = ev.mul_const(Ry, 1.0 / (double)n);
     H Cs = ev.rotsum(ev.sum(ev.hmult_v(ev.sub_v(x, mux), ev.sub_v(y, muy))));
     const int64_t pads = (int64_t)(x.size() * (size_t)ev.c.S) - (int64_t)n;
     if (pads) Cs = ev.sub(Cs, ev.mul_int(ev.hmult(mux, muy), pads));
     H cov = ev.mul_const(Cs, 1.0 / (double)n);
-    H ix = crypto_inv_sqrt(ev, variance(ev, x, n, Bx, Rx), Bx * Bx, k, t);
-    H iy = crypto_inv_sqrt(ev, variance(ev, y, n, By, Ry), By * By, k, t);
+    H ix = crypto_inv_sqrt(ev, col_var(ev, x, n, Bx, Rx, kx), Bx * Bx, k, t);
+    H iy = crypto_inv_sqrt(ev, col_var(ev, y, n, By, Ry, ky), By * By, k, t);
     return ev.hmult(ev.hmult(cov, ix), iy);
 }
 
@@ -664,11 +773,11 @@ ResObj *run_one(Ev &ev, const QueryIn &q)
     const size_t n = q.x->n;
     Col res;
     switch (q.stat) {
-    case PPST_ZSCORE: res = znorm(ev, x, n, q.o.B_x, kk, tt); break;
-    case PPST_KURT: res.push_back(kurt(ev, x, n, q.o.B_x, kk, tt)); break;
-    case PPST_SKEW: res.push_back(skew(ev, x, n, q.o.B_x, kk, tt)); break;
-    case PPST_CV: res.push_back(cv(ev, x, n, q.o.B_x, kk, tt)); break;
-    case PPST_PCC: res.push_back(pcc(ev, x, view(*q.y), n, q.o.B_x, q.o.B_y, kk, tt)); break;
+    case PPST_ZSCORE: res = znorm(ev, x, n, q.o.B_x, kk, tt, q.x); break;
+    case PPST_KURT: res.push_back(kurt(ev, x, n, q.o.B_x, kk, tt, q.x)); break;
+    case PPST_SKEW: res.push_back(skew(ev, x, n, q.o.B_x, kk, tt, q.x)); break;
+    case PPST_CV: res.push_back(cv(ev, x, n, q.o.B_x, kk, tt, q.x)); break;
+    case PPST_PCC: res.push_back(pcc(ev, x, view(*q.y), n, q.o.B_x, q.o.B_y, kk, tt, q.x, q.y)); break;
     default: throw_err(PPST_E_ARG, "unknown statistic");
     }
     ResObj *r = new ResObj();
@@ -700,7 +809,11 @@ void run_queries(Ctx &c, const EvkObj &k, const std::vector<QueryIn> &qs, std::v
     std::vector<ResObj *> res(qs.size(), nullptr);
     std::vector<std::exception_ptr> errs(qs.size());
     std::vector<std::thread> th;
-    for (size_t i = 0; i < qs.size(); i++) sched.worker_started();
+    for (size_t i = 0; i < qs.size(); i++) {
+        sched.worker_started();
+        sched.col_acquire(qs[i].x);
+        sched.col_acquire(qs[i].y);
+    }
     for (size_t i = 0; i < qs.size(); i++) {
         th.emplace_back([&, i] {
             try {
@@ -709,6 +822,8 @@ void run_queries(Ctx &c, const EvkObj &k, const std::vector<QueryIn> &qs, std::v
             } catch (...) {
                 errs[i] = std::current_exception();
             }
+            sched.col_release(qs[i].x);
+            sched.col_release(qs[i].y);
             sched.worker_finished();
         });
     }
@@ -784,6 +899,8 @@ struct Server {
             reserved += t->est;
             running++;
             sched.worker_started();
+            sched.col_acquire(t->q.x);
+            sched.col_acquire(t->q.y);
             std::thread([this, t] { work(t); }).detach();
         }
     }
@@ -801,6 +918,8 @@ struct Server {
         t->ev = e;
         // leave the scheduler before `running` drops: the destructor tears the
         // scheduler down as soon as no worker runs
+        sched.col_release(t->q.x);
+        sched.col_release(t->q.y);
         sched.worker_finished();
         std::lock_guard<std::mutex> lk(mu);
         compl_q.push_back(t);

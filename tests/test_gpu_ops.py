@@ -188,3 +188,24 @@ def test_error_codes(env):
     with pytest.raises(pp.PpstError) as e:
         ctx.drop(ga, 9)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("dnum", [1, 2, 3, 4, 6, 12])
+def test_every_digit_count(dnum):
+    """Key switching for every decomposition of a 12-prime chain (digits of
+    12, 6, 4, 3, 2 and 1 primes, K = digit size): HMult at the top level and
+    one level down, and a rotation, bit-exact against the oracle."""
+    import paper_2508_12093_gb300 as pp
+    from oracle import ckks as ock
+    prm = dict(log_n=12, n_q=12, n_p=12 // dnum, dnum=dnum, q0_bits=60, q_bits=40, p_bits=60, log_scale=40)
+    ctx = pp.Context(prm)
+    sk, evk = ctx.keygen(11, rotations=[5])
+    oc = ock.Ckks(ock.Params(**prm))
+    ok = oc.keygen(11, rotations=[5])
+    x = workloads.uniform_column(oc.prm.S, seed=3)
+    o = oc.encrypt_column(ok["pk"], x, 4)[0]
+    g = ctx.ct_import(o.c0, o.c1, o.level, o.scale)
+    same(ctx, ctx.hmult(evk, g, g), oc.hmult(o, o, ok))
+    same(ctx, ctx.hmult(evk, ctx.drop(g, 6), g), oc.hmult(oc.drop(o, 6), o, ok))
+    same(ctx, ctx.rotate(evk, g, 5), oc.rotate(o, 5, ok))
+    assert np.abs(ctx.decrypt_ct(sk, ctx.rotate(evk, g, 5)) - np.roll(x, -5)).max() < 1e-6

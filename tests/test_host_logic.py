@@ -1,0 +1,70 @@
+"""Host-side logic that needs no GPU: the replica aggregation of the
+benchmark (world size 2 over gloo), the autotuner's parameter family and its
+algorithmic byte counts, and the served-latency percentiles."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        t = bench.replica_max(1.5 + rank, dist)          # rank 1 is the slowest
+        out[rank] = (t, bench.whole_job_rate(30, world, t))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replica_aggregation_world2():
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    assert out[0] == out[1] == (2.5, 30 * 2 / 2.5)
+
+
+def test_single_rank_aggregation_is_identity():
+    import bench
+    assert bench.replica_max(3.25, None) == 3.25
+    assert bench.whole_job_rate(12, 1, 2.0) == 6.0
+
+
+def test_percentiles():
+    import bench
+    xs = list(range(1, 101))
+    assert bench.pct(xs, 50) == 51 and bench.pct(xs, 99) == 99 and bench.pct(xs, 100) == 100
+    assert bench.pct([], 50) is None
+
+
+@pytest.mark.parametrize("dnum,mb", [(3, 176.16), (4, 201.33), (6, 251.66), (12, 402.65)])
+def test_autotune_family_and_bytes(dnum, mb):
+    """K = n_q / dnum special primes; the key-switch byte counts of the N = 2^16
+    chain (two input ciphertexts, the key, the output)."""
+    import importlib.util
+    import workloads
+    # by path: the module needs the built library only to measure, not to plan
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("autotune", os.path.join(root, "paper_2508_12093_gb300", "autotune.py"))
+    autotune = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(autotune)
+    p = autotune.with_dnum(workloads.PARAMS["n16_d6"], dnum)
+    assert p["n_p"] * dnum == 24 and p["log_n"] == 16
+    assert abs(autotune.ks_bytes(p) / 1e6 - mb) < 0.01
+    with pytest.raises(ValueError):
+        autotune.with_dnum(workloads.PARAMS["n16_d6"], 5)
