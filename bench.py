@@ -331,6 +331,7 @@ def main():
     lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
 
     srv = served_stream(pp, ctx, sk, evk, ost, args.served) if args.served > 0 else None
+    e1 = inv_sqrt_sweep(ctx, sk, evk)
     peak, peak_kind = peaks()
     b64 = batched64(pp, ost, PARAMS, peak) if args.batched else None
 
@@ -410,6 +411,7 @@ def main():
                             "mode": "served stream (below)"} if srv else
                            {"p50": pct(lat_ms, 50), "p99": pct(lat_ms, 99), "mode": "one query at a time"}),
             "served": srv,
+            "inv_sqrt_sec72": e1,
             "batched64": b64,
             "hmult_ks_by_dnum": ({str(r["dnum"]): {"us": r["hmult_us"], "algorithmic_bytes": r["algorithmic_bytes"],
                                                    "frac_of_hbm": r.get("hmult_frac_of_hbm"),
@@ -450,6 +452,31 @@ def replica_max(x, dist):
 def whole_job_rate(units_per_rank, world, seconds):
     """Units processed by all replicas per second of the slowest one."""
     return units_per_rank * world / seconds
+
+
+def inv_sqrt_sweep(ctx, sk, evk):
+    """CryptoInvSqrt over the Sec. 7.2 grid (32,768 points in [0.001, 100], B = 100):
+    mean relative error of 1/sqrt(x) and GPU time, for the paper's approximation
+    settings (degree 2^9 - 1, 6 Newton steps) and the statistics' default."""
+    import numpy as np
+    import torch
+    x = workloads.inv_sqrt_grid()
+    col = ctx.encrypt_column(evk, x / 100.0, 5)
+    ref = 1.0 / np.sqrt(x)
+    out = {"grid": "16384 points in [0.001, 1] + 16384 in [1, 100], B = 100, one ciphertext",
+           "paper_mre_context": 5.08e-5}
+    for k, t in ((9, 6), (7, 3)):
+        ctx.inv_sqrt(evk, col.cts()[0], 100.0, k, t)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = ctx.inv_sqrt(evk, col.cts()[0], 100.0, k, t)
+        e1.record()
+        torch.cuda.synchronize()
+        y = ctx.decrypt_ct(sk, r)
+        out[f"deg{(1 << k) - 1}_newton{t}"] = {"mre": float(np.mean(np.abs(y - ref) / ref)),
+                                               "max_rel": float(np.max(np.abs(y - ref) / ref)),
+                                               "ms": e0.elapsed_time(e1)}
+    return out
 
 
 def pct(xs, p):

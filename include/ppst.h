@@ -232,9 +232,20 @@ int ppst_lin_comb(ppst_ctx *ctx, const ppst_ct *const *cts, const double *coeffs
                   ppst_ct **out);
 /* Keep limbs 0..level. */
 int ppst_drop(ppst_ctx *ctx, const ppst_ct *a, uint32_t level, ppst_ct **out);
+/* CryptoInvSqrt(v, C) (Sec. 5: Alg. 2 with n = 2, Alg. 3, Eq. 1, Eq. 3) on
+ * every slot: the degree 2^cheb_log2deg - 1 Chebyshev interpolant of
+ * 1 / (sqrt(C) sqrt(u + 1)) at u = v - 1, then newton_steps Newton steps
+ * y <- 1.5 y - (x' y) y^2, x' = v C / 2. Approximates 1 / sqrt(C v) for v in
+ * (0, 2]; outside that domain the result is meaningless (not detectable on
+ * encrypted data). cheb_log2deg in [2, 10], newton_steps in [0, 10], C > 0.
+ * Uses cheb_log2deg + 1 + 2 newton_steps levels (cheb_log2deg >= 3);
+ * PPST_E_DEPTH when the input's level is too low. */
+int ppst_inv_sqrt(ppst_ctx *ctx, const ppst_evk *evk, const ppst_ct *v, double C, int32_t cheb_log2deg,
+                  int32_t newton_steps, ppst_ct **out);
 
 /* ---- serving (continuous batching) -----------------------------------------
- * A request loop on its own host thread and stream: keys stay resident, queries
+ * A request loop on its own host threads (GPU work on the context's stream):
+ * keys stay resident, queries
  * are admitted while their estimated working set fits `hbm_budget` bytes (and
  * at most `max_batch` run together), their ops are batched step by step, and
  * results are handed back by ticket. */

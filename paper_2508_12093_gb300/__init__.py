@@ -347,6 +347,10 @@ class Context:
     def rotsum(self, evk, a):
         return self._new(lib.ppst_rotsum, evk.ptr, a.ptr)
 
+    def inv_sqrt(self, evk, v, C, cheb_log2deg=7, newton_steps=3):
+        """CryptoInvSqrt: approximately 1/sqrt(C v) in every slot, v in (0, 2]."""
+        return self._new(lib.ppst_inv_sqrt, evk.ptr, v.ptr, float(C), int(cheb_log2deg), int(newton_steps))
+
     def rescale(self, a):
         return self._new(lib.ppst_rescale, a.ptr)
 

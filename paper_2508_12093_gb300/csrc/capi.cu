@@ -1,4 +1,5 @@
 // capi.cu -- the extern "C" boundary (include/ppst.h).
+#include <cmath>
 #include <cstring>
 #include <new>
 
@@ -444,6 +445,19 @@ int ppst_rotsum(ppst_ctx *ctx, const ppst_evk *evk, const ppst_ct *a, ppst_ct **
         const EvkObj *k = (const EvkObj *)evk;
         REQ(ok(k, TAG_EVK), "bad key");
         *out = (ppst_ct *)ev_rotsum(*c, *k, *A);
+    })
+}
+
+int ppst_inv_sqrt(ppst_ctx *ctx, const ppst_evk *evk, const ppst_ct *a, double C, int32_t cheb_log2deg,
+                  int32_t newton_steps, ppst_ct **out)
+{
+    CT_OP(inv_sqrt, {
+        const EvkObj *k = (const EvkObj *)evk;
+        REQ(ok(k, TAG_EVK) && k->ctx == c, "bad key");
+        REQ(cheb_log2deg >= 2 && cheb_log2deg <= 10, "cheb_log2deg out of range [2, 10]");
+        REQ(newton_steps >= 0 && newton_steps <= 10, "newton_steps out of range [0, 10]");
+        REQ(C > 0 && std::isfinite(C), "C must be positive");
+        *out = (ppst_ct *)ev_inv_sqrt(*c, *k, *A, C, cheb_log2deg, newton_steps);
     })
 }
 

@@ -309,6 +309,7 @@ struct QueryIn {
 };
 void run_queries(Ctx &c, const EvkObj &k, const std::vector<QueryIn> &qs, std::vector<ResObj *> &out);
 void validate_query(const Ctx &c, const QueryIn &q);  // PPST_E_ARG on a malformed query
+CtObj *ev_inv_sqrt(Ctx &c, const EvkObj &k, const CtObj &v, double C, int cheb_log2deg, int newton_steps);
 // PPST_E_CUDA if a kernel reported a timed-out wait (the word is then cleared);
 // call once the work in question has completed
 void check_device_error(Ctx &c);

@@ -454,10 +454,10 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
         });
         check_launch("k_modup_cols");
     }
-    // per target limb and item: one digit word and two key words per digit read,
-    // two accumulators written (the key is counted once per item: the batch
-    // shares its reads through L2)
-    ProfScope _ps(c, "inner_chunks", (uint64_t)B * E_ext * (3 * nd + 2));
+    // per target limb: the two key words of every digit, read once for the
+    // batch (its items run back to back on the same key tile); per item and
+    // target limb: one digit word per digit read, two accumulators written
+    ProfScope _ps(c, "inner_chunks", (uint64_t)E_ext * 2 * nd + (uint64_t)B * E_ext * (nd + 2));
     dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
         const dim3 grid(B * ((c.N >> S) / PassShape<S>::SUB), E_ext);

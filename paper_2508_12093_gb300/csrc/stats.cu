@@ -798,6 +798,18 @@ void free_res(ResObj *r)
 
 }  // namespace
 
+CtObj *ev_inv_sqrt(Ctx &c, const EvkObj &k, const CtObj &v, double C, int cheb_log2deg, int newton_steps)
+{
+    Ev ev{c, k};
+    H in(new Holder(const_cast<CtObj *>(&v)), [](Holder *p) {
+        p->ct = nullptr;  // the caller keeps the input
+        delete p;
+    });
+    H r = crypto_inv_sqrt(ev, in, C, cheb_log2deg, newton_steps);
+    if (r == in) return ct_clone(v);
+    return r->release();
+}
+
 void run_queries(Ctx &c, const EvkObj &k, const std::vector<QueryIn> &qs, std::vector<ResObj *> &out)
 {
     if (qs.size() <= 1) {
