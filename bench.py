@@ -40,6 +40,10 @@ WORKLOAD = ("N=2^16 (32768 slots), 24 Q primes (60+23x50 bit) + 4 special 60-bit
 # (2 x 2 x 24 limbs), the relinearisation key (6 x 2 x 28 limbs) and the output
 # (2 x 24 limbs) of 2^16 words each
 HMULT_BYTES = (2 * 2 * 24 + 6 * 2 * 28 + 2 * 24) * 65536 * 8
+# DRAM bytes per algorithmic byte of a kernel, from one ncu capture of a
+# single-item top-level HMult (python -m paper_2508_12093_gb300.profcase hmult):
+# k_inner_chunks read 293.6 MB and wrote 21.7 MB against 293.6 MB algorithmic
+DRAM_PER_ALG = {"inner_chunks": (293.6 + 21.7) / 293.6}
 
 
 def peaks():
@@ -332,6 +336,7 @@ def main():
 
     srv = served_stream(pp, ctx, sk, evk, ost, args.served) if args.served > 0 else None
     e1 = inv_sqrt_sweep(ctx, sk, evk)
+    toy = toy_zscore(pp, ost)
     peak, peak_kind = peaks()
     b64 = batched64(pp, ost, PARAMS, peak) if args.batched else None
 
@@ -412,6 +417,7 @@ def main():
                            {"p50": pct(lat_ms, 50), "p99": pct(lat_ms, 99), "mode": "one query at a time"}),
             "served": srv,
             "inv_sqrt_sec72": e1,
+            "toy12_zscore": toy,
             "batched64": b64,
             "hmult_ks_by_dnum": ({str(r["dnum"]): {"us": r["hmult_us"], "algorithmic_bytes": r["algorithmic_bytes"],
                                                    "frac_of_hbm": r.get("hmult_frac_of_hbm"),
@@ -420,7 +426,11 @@ def main():
             "hmult_ks": {"us": hmult_us, "algorithmic_bytes": HMULT_BYTES, "achieved_gbs": hmult_gbs,
                          "frac_of_hbm": hmult_gbs / peak},
             "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak if achieved else None, "traffic": None,
+                         "frac": achieved / peak if achieved else None,
+                         "traffic": (DRAM_PER_ALG[dom] * alg_bytes / max(1, n_dom)) if dom in DRAM_PER_ALG else None,
+                         "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one single-item "
+                                            "top-level launch, scaled by the algorithmic bytes per launch"
+                                            if dom in DRAM_PER_ALG else None),
                          "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback",
                          "launches": n_dom, "avg_launch_us": 1000.0 * ms_dom / max(1, n_dom),
@@ -476,6 +486,38 @@ def inv_sqrt_sweep(ctx, sk, evk):
         out[f"deg{(1 << k) - 1}_newton{t}"] = {"mre": float(np.mean(np.abs(y - ref) / ref)),
                                                "max_rel": float(np.max(np.abs(y - ref) / ref)),
                                                "ms": e0.elapsed_time(e1)}
+    return out
+
+
+def toy_zscore(pp, ost):
+    """The N = 2^12 toy set: Z-score (B = 0.29, Chebyshev degree 7, 2 Newton steps)
+    of 2048 uniform values, one query at a time through ppst_query and through a
+    prepared query (the program captured once as a CUDA graph, then replayed)."""
+    import numpy as np
+    import torch
+    prm = workloads.PARAMS["toy12"]
+    ctx = pp.Context(prm)
+    sk, evk = ctx.keygen(2)
+    x = workloads.uniform_column(1 << (prm["log_n"] - 1), seed=1)
+    col = ctx.encrypt_column(evk, x, 3)
+    opts = dict(B_x=0.29, cheb_log2deg=3, newton_steps=2)
+    plan = ctx.prepare(evk, "zscore", col, None, opts)
+    ref = ost.plain_stats(x)["znorm"]
+    v, rep = ctx.decrypt(sk, plan.run())
+    err = float(np.abs(v - ref).max() / np.abs(ref).max())
+    out = {"workload": "N=2^12, 12 Q primes (60 + 11 x 40 bit) + 1 special, Z-score of 2048 uniform values",
+           "max_rel_err_vs_fp64": err, "depth_used": rep["depth_used"]}
+    for name, fn in (("query", lambda: ctx.query(evk, "zscore", col, None, opts)), ("graph", plan.run)):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        reps = 50
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        out[name + "_queries_per_s"] = reps / (time.perf_counter() - t0)
+    ctx.close()
     return out
 
 

@@ -56,6 +56,7 @@ typedef struct ppst_ct ppst_ct;       /* one ciphertext (GPU, evaluation domain)
 typedef struct ppst_col ppst_col;     /* encrypted column: ceil(n / (N/2)) cts + n  */
 typedef struct ppst_res ppst_res;     /* encrypted statistic result + depth report  */
 typedef struct ppst_server ppst_server; /* continuous-batching request loop        */
+typedef struct ppst_plan ppst_plan;     /* a query captured as a CUDA graph         */
 
 /* Parameter set (the paper fixes only N, Delta and logPQ, Sec. 7.1). Prime
  * chain rule: every prime is 1 mod 2N; q_0 is the largest prime below
@@ -242,6 +243,18 @@ int ppst_drop(ppst_ctx *ctx, const ppst_ct *a, uint32_t level, ppst_ct **out);
  * PPST_E_DEPTH when the input's level is too low. */
 int ppst_inv_sqrt(ppst_ctx *ctx, const ppst_evk *evk, const ppst_ct *v, double C, int32_t cheb_log2deg,
                   int32_t newton_steps, ppst_ct **out);
+
+/* ---- prepared queries ---------------------------------------------------------
+ * ppst_query_prepare runs the statistic program once (which sizes a private
+ * key-switch workspace), then captures it as a CUDA graph; each ppst_plan_run
+ * replays the graph (one launch on the context's stream) and returns a new
+ * result, identical to ppst_query's for the same inputs. The plan keeps its
+ * columns' device buffers alive and holds its own workspace and intermediates
+ * until ppst_free(plan). Errors as ppst_query; PPST_E_STATE if the program
+ * needed a new device allocation during the capture. */
+int ppst_query_prepare(ppst_ctx *ctx, const ppst_evk *evk, ppst_stat stat, const ppst_col *x, const ppst_col *y,
+                       const ppst_qopts *opts, ppst_plan **out);
+int ppst_plan_run(ppst_plan *plan, ppst_res **out);
 
 /* ---- serving (continuous batching) -----------------------------------------
  * A request loop on its own host threads (GPU work on the context's stream):

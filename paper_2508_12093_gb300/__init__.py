@@ -161,6 +161,21 @@ class Server(_Handle):
         return s.value
 
 
+class Plan(_Handle):
+    """A query captured as a CUDA graph (Context.prepare); run() replays it."""
+
+    def __init__(self, ctx, ptr, rows):
+        super().__init__(ctx, ptr)
+        self.rows = rows
+
+    def run(self):
+        out = ctypes.c_void_p()
+        self.ctx._check(lib.ppst_plan_run(self.ptr, ctypes.byref(out)))
+        r = Result(self.ctx, out.value)
+        r.n = self.rows
+        return r
+
+
 class Context:
     """One parameter set on one GPU stream (not thread-safe)."""
 
@@ -210,7 +225,7 @@ class Context:
         if getattr(self, "ptr", None):
             live = list(getattr(self, "_live", ()))
             for h in live:
-                if isinstance(h, Server):
+                if isinstance(h, (Server, Plan)):
                     h.close()
             for h in live:
                 h.close()
@@ -294,6 +309,15 @@ class Context:
         r = Result(self, out.value)
         r.n = x.n if stat == PPST_ZSCORE else 1
         return r
+
+    def prepare(self, evk, stat, x, y=None, opts=None):
+        """The query captured as a CUDA graph: Plan.run() replays it."""
+        o = _opts(opts)
+        out = ctypes.c_void_p()
+        st = STATS.get(stat, stat)
+        self._check(lib.ppst_query_prepare(self.ptr, evk.ptr, st, x.ptr, y.ptr if y is not None else None,
+                                           ctypes.byref(o), ctypes.byref(out)))
+        return Plan(self, out.value, x.n if st == PPST_ZSCORE else 1)
 
     def query_batch(self, evk, queries):
         """queries: list of (stat, x, y_or_None, opts)."""

@@ -87,6 +87,8 @@ SIGNATURES = {
     "ppst_submit": (c_int, [c_void_p, c_int, c_void_p, c_void_p, P(ppst_qopts), P(c_u64)]),
     "ppst_wait": (c_int, [c_void_p, c_u64, c_i32, PP]),
     "ppst_ticket_latency": (c_int, [c_void_p, c_u64, P(c_double)]),
+    "ppst_query_prepare": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, P(ppst_qopts), PP]),
+    "ppst_plan_run": (c_int, [c_void_p, PP]),
     "ppst_prof_start": (c_int, [c_void_p, ctypes.c_char_p]),
     "ppst_prof_stop": (c_int, [c_void_p]),
     "ppst_prof_read": (c_int, [c_void_p, ctypes.c_char_p, P(c_u64), P(ctypes.c_double), P(c_u64)]),

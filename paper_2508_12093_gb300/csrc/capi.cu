@@ -630,6 +630,7 @@ void ppst_free(void *handle)
         break;
     }
     case TAG_SRV: server_destroy((Server *)handle); break;
+    case TAG_PLAN: plan_destroy((Plan *)handle); break;
     default: break;
     }
 }

@@ -163,8 +163,10 @@ void *Pool::get(size_t bytes)
         v.pop_back();
         cached -= bytes;
         in_use += bytes;
+        if (recording) ledger.emplace_back(p, bytes);
         return p;
     }
+    if (frozen) throw_err(PPST_E_STATE, "device allocation while a graph is being captured");
     for (int attempt = 0; attempt < 2; attempt++) {
         void *p = nullptr;
         if (has_user) {
@@ -189,6 +191,21 @@ void Pool::put(void *p, size_t bytes)
     free_[bytes].push_back(p);
     in_use -= bytes;
     cached += bytes;
+}
+
+bool Pool::withdraw(void *p, size_t bytes)
+{
+    std::lock_guard<std::recursive_mutex> lk(mu);
+    auto it = free_.find(bytes);
+    if (it == free_.end()) return false;
+    for (size_t i = 0; i < it->second.size(); i++) {
+        if (it->second[i] != p) continue;
+        it->second.erase(it->second.begin() + i);
+        cached -= bytes;
+        in_use += bytes;
+        return true;
+    }
+    return false;
 }
 
 void Pool::trim()

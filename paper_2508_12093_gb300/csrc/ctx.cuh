@@ -17,7 +17,8 @@ namespace ppst {
 // handle tags (first word of every handle, checked by the C ABI)
 enum Tag : uint32_t {
     TAG_CTX = 0x50435458u, TAG_SK = 0x50534b30u, TAG_EVK = 0x5045564bu, TAG_CT = 0x50435430u,
-    TAG_COL = 0x50434f4cu, TAG_RES = 0x50524553u, TAG_SRV = 0x50535256u, TAG_DEAD = 0xdeadbeefu
+    TAG_COL = 0x50434f4cu, TAG_RES = 0x50524553u, TAG_SRV = 0x50535256u, TAG_PLAN = 0x504c414eu,
+    TAG_DEAD = 0xdeadbeefu
 };
 
 struct Error {
@@ -33,8 +34,14 @@ struct Pool {
     std::unordered_map<size_t, std::vector<void *>> free_;
     size_t in_use = 0, cached = 0;
     std::recursive_mutex mu;  // batched queries release ciphertexts from their own threads
+    // graph capture: `recording` notes every buffer handed out; `frozen` turns a
+    // request that the free lists cannot serve into PPST_E_STATE (no allocator
+    // call while a stream is being captured)
+    bool recording = false, frozen = false;
+    std::vector<std::pair<void *, size_t>> ledger;
     void *get(size_t bytes);
     void put(void *p, size_t bytes);
+    bool withdraw(void *p, size_t bytes);  // take a free buffer out of circulation
     void trim();
 };
 
@@ -314,8 +321,10 @@ CtObj *ev_inv_sqrt(Ctx &c, const EvkObj &k, const CtObj &v, double C, int cheb_l
 // call once the work in question has completed
 void check_device_error(Ctx &c);
 
-// ---- serving (stats.cu) ----
+// ---- serving and prepared queries (stats.cu) ----
 struct Server;
 void server_destroy(Server *s);
+struct Plan;
+void plan_destroy(Plan *p);
 
 }  // namespace ppst

@@ -17,6 +17,7 @@
 // to a common scale so that all Adds see equal scales; Newton's products are
 // associated (x' y)(y y) (depth 2 per step); padding slots of multi-ciphertext
 // columns are corrected with integer multiples of mu^p.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -1030,6 +1031,169 @@ struct Server {
 
 void server_destroy(Server *s) { delete s; }
 
+// ---------------------------------------------------------------------------
+// prepared queries: one statistic program captured as a CUDA graph
+// ---------------------------------------------------------------------------
+// The program runs once for real with a private key-switch workspace (which
+// sizes it and leaves every buffer the program uses in the pool's free lists),
+// then once more under stream capture with allocation frozen, so that it takes
+// exactly the same buffers. Afterwards the buffers the graph wrote are taken
+// out of circulation and kept by the plan together with the workspace and the
+// captured result; a replay is one graph launch followed by a copy of the
+// result into fresh ciphertexts. The plan keeps its input columns' device
+// buffers alive.
+struct WsState {
+    uint64_t *d2 = nullptr, *d2n = nullptr, *ext = nullptr, *acc = nullptr, *conv = nullptr, *top = nullptr;
+    int items = 0;
+    size_t bytes = 0;
+};
+
+static WsState ws_swap(Ctx &c, const WsState &in)
+{
+    WsState out{c.ws_d2, c.ws_d2n, c.ws_ext, c.ws_acc, c.ws_conv, c.ws_top, c.ws_items, c.ws_bytes};
+    c.ws_d2 = in.d2;
+    c.ws_d2n = in.d2n;
+    c.ws_ext = in.ext;
+    c.ws_acc = in.acc;
+    c.ws_conv = in.conv;
+    c.ws_top = in.top;
+    c.ws_items = in.items;
+    c.ws_bytes = in.bytes;
+    return out;
+}
+
+static void ws_release(Ctx &c, const WsState &w)
+{
+    if (!w.d2) return;
+    const size_t N = c.N, q = c.L + 1, e = c.ext_rows(), B = (size_t)w.items;
+    c.pool.put(w.d2, B * q * N * 8);
+    c.pool.put(w.d2n, B * q * N * 8);
+    c.pool.put(w.ext, B * c.dnum * e * N * 8);
+    c.pool.put(w.acc, B * 2 * e * N * 8);
+    c.pool.put(w.conv, B * 2 * q * N * 8);
+    c.pool.put(w.top, B * 2 * N * 8);
+}
+
+struct Plan {
+    uint32_t tag = TAG_PLAN;
+    Ctx *c = nullptr;
+    std::vector<std::shared_ptr<uint64_t>> inputs;
+    WsState ws;
+    ResObj *res = nullptr;
+    std::vector<std::pair<void *, size_t>> retained;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t launches = 0;  // kernels per replay
+
+    ~Plan()
+    {
+        if (!c) return;
+        cudaStreamSynchronize(c->stream);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+        free_res(res);
+        for (auto &b : retained) c->pool.put(b.first, b.second);
+        ws_release(*c, ws);
+        tag = TAG_DEAD;
+    }
+};
+
+static CtObj *ct_copy(Ctx &c, const CtObj &a)
+{
+    CtObj *o = ct_new(c, a.level, a.scale);
+    const size_t words = (size_t)(a.level + 1) * c.N, ps = (size_t)(c.L + 1) * c.N;
+    k_copy(c, o->d, a.d, words);
+    k_copy(c, o->d + ps, a.d + ps, words);
+    return o;
+}
+
+Plan *plan_create(Ctx &c, const EvkObj &k, const QueryIn &q)
+{
+    std::unique_ptr<Plan> pl(new Plan());
+    pl->c = &c;
+    for (const CtObj *ct : q.x->cts) pl->inputs.push_back(ct->buf);
+    if (q.y)
+        for (const CtObj *ct : q.y->cts) pl->inputs.push_back(ct->buf);
+    const bool prof_on = c.prof.on;
+    const cudaStream_t s0 = c.stream;
+    WsState user = ws_swap(c, WsState{});  // the program gets a workspace of its own
+    auto restore = [&] {
+        c.pool.recording = c.pool.frozen = false;
+        c.pool.ledger.clear();
+        c.stream = s0;
+        c.prof.on = prof_on;
+        pl->ws = ws_swap(c, user);
+    };
+    try {
+        c.prof.on = false;
+        {
+            Ev ev{c, k};
+            free_res(run_one(ev, q));
+        }
+        PPST_CUDA(cudaStreamSynchronize(s0));  // the warm-up's buffers are idle before the capture
+        PPST_CUDA(cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking));
+        c.stream = pl->cap;
+        c.pool.ledger.clear();
+        c.pool.recording = c.pool.frozen = true;
+        const uint64_t l0 = c.prof.launches;  // captured launches do not run: not counted
+        PPST_CUDA(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
+        ResObj *r = nullptr;
+        std::exception_ptr err;
+        try {
+            Ev ev{c, k};
+            r = run_one(ev, q);
+        } catch (...) {
+            err = std::current_exception();
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(pl->cap, &g);
+        c.prof.launches = l0;
+        pl->graph = g;
+        pl->res = r;
+        if (err) std::rethrow_exception(err);
+        if (ce != cudaSuccess || !g) throw_err(PPST_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        PPST_CUDA(cudaGraphInstantiate(&pl->exec, g, 0));
+        size_t nodes = 0;
+        PPST_CUDA(cudaGraphGetNodes(g, nullptr, &nodes));  // kernel nodes only: the program copies nothing
+        pl->launches = nodes;
+        // the intermediates the graph wrote stay with it (each buffer once)
+        std::vector<std::pair<void *, size_t>> led = c.pool.ledger;
+        std::sort(led.begin(), led.end());
+        led.erase(std::unique(led.begin(), led.end()), led.end());
+        for (auto &b : led)
+            if (c.pool.withdraw(b.first, b.second)) pl->retained.push_back(b);
+        restore();
+    } catch (...) {
+        cudaGetLastError();
+        restore();
+        throw;
+    }
+    return pl.release();
+}
+
+ResObj *plan_run(Plan &pl)
+{
+    Ctx &c = *pl.c;
+    PPST_CUDA(cudaGraphLaunch(pl.exec, c.stream));
+    c.prof.launches += pl.launches;
+    std::unique_ptr<ResObj> out(new ResObj());
+    out->ctx = &c;
+    out->stat = pl.res->stat;
+    out->n = pl.res->n;
+    out->level_in = pl.res->level_in;
+    try {
+        for (const CtObj *ct : pl.res->cts) out->cts.push_back(ct_copy(c, *ct));
+    } catch (...) {
+        for (CtObj *ct : out->cts) ct_free(ct);
+        throw;
+    }
+    return out.release();
+}
+
+void plan_destroy(Plan *p) { delete p; }
+
 }  // namespace ppst
 
 using namespace ppst;
@@ -1087,6 +1251,52 @@ int ppst_wait(ppst_server *srv, uint64_t ticket, int32_t timeout_ms, ppst_res **
         return s->c->fail(e.code, e.msg);
     } catch (...) {
         return PPST_E_ARG;
+    }
+}
+
+int ppst_query_prepare(ppst_ctx *ctx, const ppst_evk *evk, ppst_stat stat, const ppst_col *x, const ppst_col *y,
+                       const ppst_qopts *opts, ppst_plan **out)
+{
+    Ctx *c = (Ctx *)ctx;
+    const EvkObj *k = (const EvkObj *)evk;
+    if (!c || c->tag != TAG_CTX || !out) return PPST_E_ARG;
+    *out = nullptr;
+    if (!k || k->tag != TAG_EVK || k->ctx != c) return c->fail(PPST_E_ARG, "bad key");
+    try {
+        std::lock_guard<std::recursive_mutex> lk(c->exec_mu);
+        QueryIn q;
+        q.stat = stat;
+        q.x = (const ColObj *)x;
+        q.y = (const ColObj *)y;
+        q.o = opts ? *opts : ppst_qopts{1.0, 1.0, 7, 3};
+        validate_query(*c, q);
+        *out = (ppst_plan *)plan_create(*c, *k, q);
+        c->clear_err();
+        return PPST_OK;
+    } catch (const PpstError &e) {
+        return c->fail(e.code, e.msg);
+    } catch (const std::bad_alloc &) {
+        return c->fail(PPST_E_OOM, "host allocation failed");
+    } catch (...) {
+        return c->fail(PPST_E_ARG, "unexpected error");
+    }
+}
+
+int ppst_plan_run(ppst_plan *plan, ppst_res **out)
+{
+    Plan *p = (Plan *)plan;
+    if (!p || p->tag != TAG_PLAN || !out) return PPST_E_ARG;
+    *out = nullptr;
+    Ctx *c = p->c;
+    try {
+        std::lock_guard<std::recursive_mutex> lk(c->exec_mu);
+        *out = (ppst_res *)plan_run(*p);
+        c->clear_err();
+        return PPST_OK;
+    } catch (const PpstError &e) {
+        return c->fail(e.code, e.msg);
+    } catch (...) {
+        return c->fail(PPST_E_OOM, "result allocation failed");
     }
 }
 
