@@ -240,6 +240,8 @@ void ntt_fwd(Ctx &c, const LimbMap &m);
 void ntt_inv(Ctx &c, const LimbMap &m);
 // inverse NTT whose final N^-1 is replaced by outmul[b] (N^-1 times a per-limb constant)
 void ntt_inv_mul(Ctx &c, const LimbMap &m, const Tw *outmul);
+// the last (COLS) pass only, for limbs whose CHUNKS pass ran fused into another kernel
+void ntt_inv_cols_mul(Ctx &c, const LimbMap &m, const Tw *outmul);
 LimbMap map_ct(const Ctx &c, uint64_t *d, int level);  // both polys of a ciphertext buffer
 LimbMap map_poly(const Ctx &c, uint64_t *d, int level); // one poly, limbs 0..level
 

@@ -3,7 +3,8 @@
 // Key switching of d (level l, dnum digits of alpha primes, K special primes)
 // is computed as three fused stages, none of which writes an evaluation-domain
 // digit to HBM:
-//   1. inverse NTT of d whose final N^-1 carries (Q_j / q_i)^-1 of the limb's
+//   1. inverse NTT of d, its first pass fused into the tensor product (or the
+//      automorphism), its final N^-1 carrying (Q_j / q_i)^-1 of the limb's
 //      digit: the first factor of ModUp's base conversion comes for free;
 //   2. k_modup_cols: for every digit j and target limb e outside it, the load
 //      of the COLS transform pass computes the base conversion
@@ -56,52 +57,83 @@ static inline Ws ws_strides(const Ctx &c)
 // ---------------------------------------------------------------------------
 // 0. batched tensor / automorphism into the key-switch input buffers
 // ---------------------------------------------------------------------------
-// d0, d1 -> t[item]; d2 -> d2n[item] and d2[item]
-__global__ void __launch_bounds__(256) k_tensor_b(ItemPtrs ip, uint64_t *__restrict__ d2,
-                                                  uint64_t *__restrict__ d2n, const PrimeC *__restrict__ pc, int N,
-                                                  int nl, size_t pstride, size_t d2_stride)
+// tensor (d0, d1 -> t[item]; d2 -> d2n[item] and, after the pass, d2[item]) and
+// automorphism (sigma_g(c0) -> out[item].c0; sigma_g(c1) -> d2n[item], d2[item]),
+// each fused with the first (CHUNKS) pass of the inverse transform of d2: a block
+// owns SUB chunks of one limb, so each thread's E words (stored at h + T k,
+// natural E h + k) are exactly what the inverse CHUNKS pass takes; d2 leaves in
+// that pass's output layout for the COLS pass.
+template <int S>
+__global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS)
+    k_tensor_ic(ItemPtrs ip, uint64_t *__restrict__ d2, uint64_t *__restrict__ d2n, const PrimeC *__restrict__ pc,
+                const Tw *__restrict__ twi, int logN, int nl, size_t pstride, size_t d2_stride)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
+    typedef PassShape<S> P;
+    __shared__ uint64_t sm[P::SMEM_WORDS];
+    const int N = 1 << logN;
     const int it = blockIdx.y / nl, i = blockIdx.y - it * nl;
     const PrimeC p = pc[i];
-    const size_t off = (size_t)i * N + c;
+    int h, sub;
+    pass_coords<S, false>(h, sub);
+    const int g = blockIdx.x * P::SUB + sub;
+    const size_t base = (size_t)i * N + (size_t)g * P::M + h;
     const uint64_t *a = ip.in0[it], *b = ip.in1[it];
     uint64_t *t = ip.out[it];
-    const uint64_t x0 = a[off], x1 = a[pstride + off], y0 = b[off], y1 = b[pstride + off];
-    t[off] = mul_mod(x0, y0, p);
-    const uint64_t v2 = mul_mod(x1, y1, p);
-    d2n[it * d2_stride + off] = v2;
-    d2[it * d2_stride + off] = v2;
-    Acc128 acc{0, 0};
-    mac(acc, x0, y1);
-    mac(acc, x1, y0);
-    t[pstride + off] = mont_mul(mont_redc(acc.hi, acc.lo, p.q, p.qinv), p.r2, p.q, p.qinv);
+    uint64_t x[P::E];
+#pragma unroll
+    for (int k = 0; k < P::E; k++) {
+        const size_t off = base + P::T * k;
+        const uint64_t x0 = a[off], x1 = a[pstride + off], y0 = b[off], y1 = b[pstride + off];
+        t[off] = mul_mod(x0, y0, p);
+        x[k] = mul_mod(x1, y1, p);
+        d2n[it * d2_stride + off] = x[k];
+        Acc128 acc{0, 0};
+        mac(acc, x0, y1);
+        mac(acc, x1, y0);
+        t[pstride + off] = mont_mul(mont_redc(acc.hi, acc.lo, p.q, p.qinv), p.r2, p.q, p.qinv);
+    }
+    chunks_inv_core<S>(x, sm, h, sub, g, N, twi + (size_t)i * N, p.q);
+    uint64_t *o = d2 + it * d2_stride + base;
+#pragma unroll
+    for (int k = 0; k < P::E; k++) o[P::T * k] = x[k];
 }
 
-// sigma_g(c0) -> out[item].c0; sigma_g(c1) -> d2n[item] and d2[item] (evaluation domain permutation)
-__global__ void __launch_bounds__(256) k_automorph_b(ItemPtrs ip, uint64_t *__restrict__ d2,
-                                                     uint64_t *__restrict__ d2n, int logN, int nl, uint64_t g,
-                                                     size_t pstride, size_t d2_stride)
+// blockIdx.y = (item, poly, limb): poly 0 -> out[item].c0, poly 1 -> d2n and (after the pass) d2
+template <int S>
+__global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS)
+    k_automorph_ic(ItemPtrs ip, uint64_t *__restrict__ d2, uint64_t *__restrict__ d2n, const PrimeC *__restrict__ pc,
+                   const Tw *__restrict__ twi, int logN, int nl, uint64_t gal, size_t pstride, size_t d2_stride)
 {
+    typedef PassShape<S> P;
+    __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
     const int row = blockIdx.y, it = row / (2 * nl), r2 = row - it * 2 * nl, poly = r2 / nl, i = r2 - poly * nl;
-    // output address k holds natural word n; sigma_g moves the evaluation at
-    // psi^(2 brv(n) + 1) from psi^(g (2 brv(n) + 1))
-    const uint32_t n = eval_natural((uint32_t)k, logN);
-    const uint32_t bk = __brev(n) >> (32 - logN);
-    const uint64_t e = ((2ull * bk + 1) * g) & (2ull * N - 1);
-    const uint32_t src = eval_address(__brev((uint32_t)((e - 1) >> 1)) >> (32 - logN), logN);
+    int h, sub;
+    pass_coords<S, false>(h, sub);
+    const int g = blockIdx.x * P::SUB + sub;
     const size_t o = (size_t)i * N;
-    const uint64_t v = ip.in0[it][(size_t)poly * pstride + o + src];
-    if (poly == 0) {
-        ip.out[it][o + k] = v;
-    } else {
-        d2n[it * d2_stride + o + k] = v;
-        d2[it * d2_stride + o + k] = v;
+    const uint64_t *src = ip.in0[it] + (size_t)poly * pstride + o;
+    uint64_t x[P::E];
+#pragma unroll
+    for (int k = 0; k < P::E; k++) {
+        // output address g M + h + T k holds natural word n = g M + E h + k; sigma_g moves
+        // the evaluation at psi^(2 brv(n) + 1) from psi^(g (2 brv(n) + 1))
+        const uint32_t n = (uint32_t)(g * P::M + P::E * h + k);
+        const uint32_t bk = __brev(n) >> (32 - logN);
+        const uint64_t e = ((2ull * bk + 1) * gal) & (2ull * N - 1);
+        x[k] = src[eval_address(__brev((uint32_t)((e - 1) >> 1)) >> (32 - logN), logN)];
     }
+    const size_t base = o + (size_t)g * P::M + h;
+    if (poly == 0) {  // block-uniform
+#pragma unroll
+        for (int k = 0; k < P::E; k++) ip.out[it][base + P::T * k] = x[k];
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < P::E; k++) d2n[it * d2_stride + base + P::T * k] = x[k];
+    chunks_inv_core<S>(x, sm, h, sub, g, N, twi + (size_t)i * N, pc[i].q);
+#pragma unroll
+    for (int k = 0; k < P::E; k++) d2[it * d2_stride + base + P::T * k] = x[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -431,12 +463,13 @@ static dim3 grid_s(const Ctx &c, int S, int rows) { return dim3((c.N >> S) / 16,
 
 // stages 1-3 for B items: d (limbs 0..level) of item b in the evaluation domain
 // in ws_d2n[b] and (to be transformed) in ws_d2[b]; accumulators to ws_acc[b]
+// d2 (every item) has been through the first inverse pass (k_tensor_ic / k_automorph_ic)
 static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
 {
     const Ws ws = ws_strides(c);
     const int nd = c.ndigits(level), E_ext = level + 1 + c.K;
     LimbMap md{c.ws_d2, ws.d2, level + 1, B, level + 1, 0, 0};
-    ntt_inv_mul(c, md, c.d_modup_outmul + c.modup_outmul_off[level]);
+    ntt_inv_cols_mul(c, md, c.d_modup_outmul + c.modup_outmul_off[level]);
     DigitOffs offs;
     for (int j = 0; j < nd; j++) offs.off[j] = c.modup_off[level][j];
     const size_t es = c.ext_rows() * c.N;
@@ -554,10 +587,13 @@ std::vector<CtObj *> ev_hmult_batch(Ctx &c, const EvkObj &k, const std::vector<c
             ip.out[i] = t[i]->d;
         }
         {
-            ProfScope _ps(c, "tensor", (uint64_t)B * 8 * (lv + 1));
-            k_tensor_b<<<dim3(c.N / 256, B * (lv + 1)), 256, 0, c.stream>>>(ip, c.ws_d2, c.ws_d2n, c.d_pc, c.N,
-                                                                              lv + 1, ps, ws.d2);
-            check_launch("k_tensor_b");
+            ProfScope _ps(c, "tensor", (uint64_t)B * 7 * (lv + 1));
+            dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
+                constexpr int S = decltype(sv)::value;
+                k_tensor_ic<S><<<dim3((c.N >> S) / PassShape<S>::SUB, B * (lv + 1)), PassShape<S>::THREADS, 0,
+                                 c.stream>>>(ip, c.ws_d2, c.ws_d2n, c.d_pc, c.d_twi, c.logN, lv + 1, ps, ws.d2);
+            });
+            check_launch("k_tensor_ic");
         }
         ks_modup_inner(c, lv, k.relin, B);
         ItemPtrs op{};
@@ -609,9 +645,13 @@ std::vector<CtObj *> ev_rotate_batch(Ctx &c, const EvkObj &k, const std::vector<
         }
         {
             ProfScope _ps(c, "automorph", (uint64_t)B * 5 * (lv + 1));
-            k_automorph_b<<<dim3(c.N / 256, B * 2 * (lv + 1)), 256, 0, c.stream>>>(
-                ip, c.ws_d2, c.ws_d2n, c.logN, lv + 1, galois_elt(c, rr), ps, ws.d2);
-            check_launch("k_automorph_b");
+            dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
+                constexpr int S = decltype(sv)::value;
+                k_automorph_ic<S><<<dim3((c.N >> S) / PassShape<S>::SUB, B * 2 * (lv + 1)), PassShape<S>::THREADS,
+                                    0, c.stream>>>(ip, c.ws_d2, c.ws_d2n, c.d_pc, c.d_twi, c.logN, lv + 1,
+                                                   galois_elt(c, rr), ps, ws.d2);
+            });
+            check_launch("k_automorph_ic");
         }
         ks_modup_inner(c, lv, it->second, B);
         ItemPtrs op{};

@@ -144,6 +144,12 @@ void ntt_inv_mul(Ctx &c, const LimbMap &m, const Tw *outmul)
         });
         check_launch("ntt_chunks_inv");
     }
+    ntt_inv_cols_mul(c, m, outmul);
+}
+
+void ntt_inv_cols_mul(Ctx &c, const LimbMap &m, const Tw *outmul)
+{
+    if (m.count() == 0) return;
     ProfScope _ps(c, "ntt_cols_inv", (uint64_t)2 * m.count());
     dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
