@@ -374,7 +374,7 @@ def main():
         nonlocal d2h
         g = ctx.ct_import(h_c0.numpy(), h_c1.numpy(), lv, sc)
         colg = ctx.col_from_cts([g], ctx.S)
-        res = [ctx.query(evk, s, colg, opts=OPTS) for s in STATS]
+        res = ctx.query_batch(evk, [(s, colg, None, OPTS) for s in STATS])
         d = 0
         for r in res:
             v, rep = ctx.decrypt(sk, r)

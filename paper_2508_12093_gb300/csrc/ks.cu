@@ -411,48 +411,80 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
 // CHUNKS pass of z and the output combine:
 //   RESC:  out_i = d_i q_l^-1 + acc_i (P^-1 q_l^-1) - Z_i q_l^-1     (d = in0[item])
 //   else:  out_i = add_i + acc_i P^-1 - Z_i        (add = in0[item] for c0, 0 for c1)
+// The block's acc and d tiles (contiguous SUB M words each) are fetched by bulk
+// asynchronous copies issued at the start, so they arrive while z is transformed.
+template <int S>
+struct MdSmem {
+    typedef PassShape<S> P;
+    static constexpr int TILE = P::SUB * P::M;
+    static constexpr size_t A_OFF = 128;                           // acc tile
+    static constexpr size_t D_OFF = A_OFF + (size_t)TILE * 8;      // d tile
+    static constexpr size_t T_OFF = D_OFF + (size_t)TILE * 8;      // transpose buffer
+    static constexpr size_t BYTES = T_OFF + (size_t)P::SMEM_WORDS * 8;
+};
+
 template <int S, bool RESC>
 __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
     k_md_chunks(const uint64_t *__restrict__ z, const uint64_t *__restrict__ acc, ItemPtrs ip,
                 const MdC *__restrict__ mdc, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN, int nl,
-                size_t ext_stride, size_t z_stride, size_t pstride, Ws ws)
+                size_t ext_stride, size_t z_stride, size_t pstride, Ws ws, int *err)
 {
     typedef PassShape<S> P;
-    __shared__ uint64_t sm[P::SMEM_WORDS];
+    typedef MdSmem<S> SM;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    const uint64_t *at = reinterpret_cast<const uint64_t *>(smem + SM::A_OFF);
+    const uint64_t *dt = reinterpret_cast<const uint64_t *>(smem + SM::D_OFF);
+    uint64_t *sm = reinterpret_cast<uint64_t *>(smem + SM::T_OFF);
+    constexpr uint32_t TB = SM::TILE * 8;
     const int N = 1 << logN;
     const int it = blockIdx.y / (2 * nl), rem = blockIdx.y - it * 2 * nl;
     const int k = rem / nl, i = rem - k * nl;
     const PrimeC p = pc[i];
     const MdC mc = mdc[i];
+    const size_t t0 = (size_t)i * N + (size_t)blockIdx.x * SM::TILE;  // the block's tile in a polynomial
+    const uint64_t *ad = (RESC || k == 0) ? ip.in0[it] + (size_t)k * pstride : nullptr;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_fence_init();
+        mbar_arrive_expect_tx(&bar[0], ad ? 2 * TB : TB);
+        bulk_g2s(smem + SM::A_OFF, acc + it * ws.acc + (size_t)k * ext_stride + t0, TB, &bar[0]);
+        if (ad) bulk_g2s(smem + SM::D_OFF, ad + t0, TB, &bar[0]);
+    }
+    __syncthreads();
     int h, sub;
     pass_coords<S, false>(h, sub);
     const int g = blockIdx.x * P::SUB + sub;
+    const int w0 = sub * P::M + h;  // this thread's words of a tile: w0 + T kk (natural E h + kk)
     uint64_t x[P::E];
-    const uint64_t *src = z + it * ws.conv + (size_t)k * z_stride + (size_t)i * N + (size_t)g * P::M;
+    const uint64_t *src = z + it * ws.conv + (size_t)k * z_stride + t0 + w0;
 #pragma unroll
-    for (int kk = 0; kk < P::E; kk++) x[kk] = src[h + P::T * kk];
+    for (int kk = 0; kk < P::E; kk++) x[kk] = src[P::T * kk];
     chunks_fwd_core<S>(x, sm, h, sub, g, N, tw + (size_t)i * N, p.q);
-    // natural word E h + kk of the chunk is stored at fin + T kk
-    const size_t fin = (size_t)i * N + (size_t)g * P::M + h;
-    const uint64_t *ad = (RESC || k == 0) ? ip.in0[it] + (size_t)k * pstride : nullptr;
-    uint64_t *od = ip.out[it] + (size_t)k * pstride;
-    const uint64_t *ak = acc + it * ws.acc + (size_t)k * ext_stride + fin;
+    if (__syncthreads_or(!mbar_wait(&bar[0], 0))) {  // the tiles did not arrive in time
+        if (threadIdx.x == 0) {
+            *(volatile int *)err = 1;
+            mbar_wait(&bar[0], 0);
+        }
+        return;
+    }
+    uint64_t *od = ip.out[it] + (size_t)k * pstride + t0 + w0;
 #pragma unroll
     for (int kk = 0; kk < P::E; kk++) {
         const uint64_t Z = reduce4q(x[kk], p.q);
-        const uint64_t av = ak[P::T * kk];
+        const uint64_t av = at[w0 + P::T * kk];
         uint64_t r;
         if (RESC) {
-            const uint64_t dv = ad[fin + P::T * kk];
+            const uint64_t dv = dt[w0 + P::T * kk];
             r = csub(shoup(dv, mc.qlinv.w, mc.qlinv.s, p.q), p.q);
             r = add_mod(r, csub(shoup(av, mc.pq.w, mc.pq.s, p.q), p.q), p.q);
             r = sub_mod(r, csub(shoup(Z, mc.qlinv.w, mc.qlinv.s, p.q), p.q), p.q);
         } else {
             r = csub(shoup(av, mc.pinv.w, mc.pinv.s, p.q), p.q);
-            if (ad) r = add_mod(r, ad[fin + P::T * kk], p.q);
+            if (ad) r = add_mod(r, dt[w0 + P::T * kk], p.q);
             r = sub_mod(r, Z, p.q);
         }
-        od[fin + P::T * kk] = r;
+        od[P::T * kk] = r;
     }
 }
 
@@ -556,8 +588,15 @@ static void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip)
     ProfScope _ps(c, "moddown_chunks", (uint64_t)B * (RESC ? 8 : 7) * nl);
     dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
-        k_md_chunks<S, RESC><<<grid_s(c, S, B * 2 * nl), PassShape<S>::THREADS, 0, c.stream>>>(
-            c.ws_conv, c.ws_acc, ip, mdc, c.d_pc, c.d_twf, c.logN, nl, es, ps, ps, ws);
+        const size_t smem = MdSmem<S>::BYTES;
+        static std::atomic<bool> attr_set{false};
+        if (!attr_set.load()) {
+            PPST_CUDA(cudaFuncSetAttribute(k_md_chunks<S, RESC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+            attr_set = true;
+        }
+        k_md_chunks<S, RESC><<<grid_s(c, S, B * 2 * nl), PassShape<S>::THREADS, smem, c.stream>>>(
+            c.ws_conv, c.ws_acc, ip, mdc, c.d_pc, c.d_twf, c.logN, nl, es, ps, ps, ws, c.d_err);
     });
     check_launch("k_md_chunks");
 }
