@@ -237,7 +237,7 @@ int ppst_decrypt(ppst_ctx *ctx, const ppst_sk *sk, const ppst_res *res, double *
             }
         } else {
             count = 1;
-            decrypt_to_slots(*c, *s, *r->cts[0], slots);
+            decrypt_to_slots(*c, *s, *r->cts[0], slots, 1);  // a statistic sits in slot 0 (every slot)
             if (cap) out[0] = slots[0];
         }
         if (n_out) *n_out = count;

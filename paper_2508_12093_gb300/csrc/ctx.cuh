@@ -1,6 +1,7 @@
 // ctx.cuh -- context, handles and internal entry points of the library.
 #pragma once
 #include <atomic>
+#include <complex>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -132,6 +133,7 @@ struct Ctx {
     std::vector<uint64_t> primes;  // q_0..q_L, p_0..p_{K-1}
     std::vector<PrimeC> hpc;       // host copy of the per-prime constants
     std::vector<uint64_t> psi;
+    std::vector<std::complex<double>> twist;  // zeta^i, zeta = e^(i pi / N): decoding (host)
     PrimeC *d_pc = nullptr;
     Tw *d_twf = nullptr, *d_twi = nullptr;  // [prime][N]: psi^brv(k), psi^-brv(k) with Shoup companions
     uint64_t *d_cdt = nullptr;  // discrete Gaussian CDT
@@ -305,7 +307,8 @@ uint64_t galois_elt(const Ctx &c, int r);
 void keygen(Ctx &c, uint64_t seed, const std::vector<int> &rots, SkObj *&sk, EvkObj *&evk);
 CtObj *encrypt_ints(Ctx &c, const EvkObj &k, const int64_t *m, uint64_t seed, uint32_t index, double scale);
 void encode(const Ctx &c, const double *z, size_t n, double scale, std::vector<int64_t> &m);
-void decrypt_to_slots(Ctx &c, const SkObj &sk, const CtObj &ct, std::vector<double> &slots);
+// slots of a ciphertext; want = 1: slot 0 only (the others are left 0)
+void decrypt_to_slots(Ctx &c, const SkObj &sk, const CtObj &ct, std::vector<double> &slots, int want = 0);
 void export_ct(Ctx &c, const CtObj &ct, uint64_t *c0, uint64_t *c1);
 CtObj *import_ct(Ctx &c, const uint64_t *c0, const uint64_t *c1, int level, double scale);
 void export_swk(Ctx &c, const Swk &k, int digit, uint64_t *b, uint64_t *a);

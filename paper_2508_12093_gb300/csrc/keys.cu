@@ -7,6 +7,7 @@
 // discrete Gaussian (sigma 3.2, |e| <= 19) by a cumulative table.
 #include <cmath>
 #include <complex>
+#include <thread>
 #include <cstring>
 
 #include "ctx.cuh"
@@ -254,10 +255,12 @@ struct Crt {
         for (size_t i = a.size(); i-- > 0;) r = r * 0x1p64 + (double)a[i];
         return r;
     }
+    // the centred value of the residues r[i stride] (Garner's mixed radix, then
+    // the big integer x or x - Q), as a double; no allocation
     double centred(const uint64_t *r, size_t stride) const
     {
         const int n = (int)q.size();
-        std::vector<uint64_t> v(n);
+        uint64_t v[MAXL];
         for (int i = 0; i < n; i++) {
             // x_{<i} mod q_i = sum_{k<i} v_k prod_{m<k} q_m
             uint64_t s = 0;
@@ -265,36 +268,60 @@ struct Crt {
             uint64_t d = (r[(size_t)i * stride] % q[i] + q[i] - s) % q[i];
             v[i] = h_mulmod(d, inv[i], q[i]);
         }
-        std::vector<uint64_t> x(Q.size() + 1, 0);
+        const size_t W = Q.size() + 1;
+        uint64_t x[MAXL + 2] = {0};
         for (int k = 0; k < n; k++) {  // x += v_k * big[k]
             u128 carry = 0;
-            for (size_t i = 0; i < x.size(); i++) {
-                u128 cur = (u128)x[i] + carry + (i < big[k].size() ? (u128)big[k][i] * v[k] : 0);
+            const std::vector<uint64_t> &bk = big[k];
+            for (size_t i = 0; i < W; i++) {
+                u128 cur = (u128)x[i] + carry + (i < bk.size() ? (u128)bk[i] * v[k] : 0);
                 x[i] = (uint64_t)cur;
                 carry = cur >> 64;
             }
         }
-        if (cmp(x, halfQ) > 0) {  // x - Q, negative
-            std::vector<uint64_t> d(x.size(), 0);
-            u128 borrow = 0;
-            for (size_t i = 0; i < x.size(); i++) {  // Q - x
-                u128 qi = i < Q.size() ? Q[i] : 0;
-                u128 sub = (u128)x[i] + borrow;
-                if (qi >= sub) {
-                    d[i] = (uint64_t)(qi - sub);
+        int c = 0;  // compare x with Q / 2
+        for (size_t i = W; i-- > 0 && c == 0;) {
+            const uint64_t hq = i < halfQ.size() ? halfQ[i] : 0;
+            if (x[i] != hq) c = x[i] < hq ? -1 : 1;
+        }
+        double sign = 1.0;
+        if (c > 0) {  // negative: Q - x
+            sign = -1.0;
+            uint64_t borrow = 0;
+            for (size_t i = 0; i < W; i++) {
+                const uint64_t qi = i < Q.size() ? Q[i] : 0;
+                const u128 sub = (u128)x[i] + borrow;
+                if ((u128)qi >= sub) {
+                    x[i] = (uint64_t)((u128)qi - sub);
                     borrow = 0;
                 } else {
-                    d[i] = (uint64_t)((((u128)1) << 64) + qi - sub);
+                    x[i] = (uint64_t)((((u128)1) << 64) + qi - sub);
                     borrow = 1;
                 }
             }
-            return -to_double(d);
         }
-        return to_double(x);
+        double r0 = 0;
+        for (size_t i = W; i-- > 0;) r0 = r0 * 0x1p64 + (double)x[i];
+        return sign * r0;
     }
 };
 
-void decrypt_to_slots(Ctx &c, const SkObj &sk, const CtObj &ct, std::vector<double> &slots)
+// m_i / scale for every coefficient i, on up to 16 host threads
+static void crt_scaled(const Crt &crt, const uint64_t *h, int N, double scale, std::vector<double> &m)
+{
+    m.resize(N);
+    const int T = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    auto work = [&](int t) {
+        for (int i = (int)((int64_t)N * t / T); i < (int)((int64_t)N * (t + 1) / T); i++)
+            m[i] = crt.centred(h + i, (size_t)N) / scale;
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < T; t++) th.emplace_back(work, t);
+    work(0);
+    for (std::thread &x : th) x.join();
+}
+
+void decrypt_to_slots(Ctx &c, const SkObj &sk, const CtObj &ct, std::vector<double> &slots, int want)
 {
     const int N = c.N, nl = ct.level + 1;
     Scratch si(c, (size_t)N * 8), sr(c, (size_t)nl * N * 8), mr(c, (size_t)nl * N * 8);
@@ -310,11 +337,21 @@ void decrypt_to_slots(Ctx &c, const SkObj &sk, const CtObj &ct, std::vector<doub
     PPST_CUDA(cudaStreamSynchronize(c.stream));
     check_device_error(c);
     Crt crt(std::vector<uint64_t>(c.primes.begin(), c.primes.begin() + nl));
-    std::vector<std::complex<double>> v(N);
-    for (int i = 0; i < N; i++) {
-        const double mi = crt.centred(h.data() + i, (size_t)N) / ct.scale;
-        v[i] = std::complex<double>(mi, 0.0) * std::complex<double>(std::cos(M_PI * i / N), std::sin(M_PI * i / N));
+    std::vector<double> m;
+    crt_scaled(crt, h.data(), N, ct.scale, m);
+    if (c.twist.size() != (size_t)N) {
+        c.twist.resize(N);
+        for (int i = 0; i < N; i++) c.twist[i] = std::complex<double>(std::cos(M_PI * i / N), std::sin(M_PI * i / N));
     }
+    if (want == 1) {  // slot 0 alone: m(zeta) = sum_i m_i zeta^i, real part
+        double s0 = 0;
+        for (int i = 0; i < N; i++) s0 += m[i] * c.twist[i].real();
+        slots.assign(c.S, 0.0);
+        slots[0] = s0;
+        return;
+    }
+    std::vector<std::complex<double>> v(N);
+    for (int i = 0; i < N; i++) v[i] = m[i] * c.twist[i];
     fft_inplace(v, +1);
     slots.resize(c.S);
     const uint64_t M = 2ull * N;

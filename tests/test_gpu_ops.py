@@ -188,6 +188,16 @@ def test_error_codes(env):
     with pytest.raises(pp.PpstError) as e:
         ctx.drop(ga, 9)
     assert e.value.code == -1
+    with pytest.raises(pp.PpstError) as e:  # an empty column
+        ctx.encrypt_column(evk, np.zeros(0), 1)
+    assert e.value.code == -1
+    with pytest.raises(pp.PpstError) as e:  # a non-finite value cannot be encoded
+        ctx.encrypt_column(evk, np.array([1.0, np.nan]), 1)
+    assert e.value.code == -1
+    for bad in (dict(SMALL, log_n=9), dict(SMALL, n_q=1), dict(SMALL, dnum=7), dict(SMALL, n_p=17)):
+        with pytest.raises(pp.PpstError) as e:
+            pp.Context(bad)
+        assert e.value.code == -1
 
 
 @pytest.mark.parametrize("dnum", [1, 2, 3, 4, 6, 12])

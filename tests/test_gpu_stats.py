@@ -43,7 +43,7 @@ def check_same(ctx, g, o):
     assert np.array_equal(c0, o.c0) and np.array_equal(c1, o.c1)
 
 
-@pytest.mark.parametrize("n", [2048, 2048 + 301, 1])
+@pytest.mark.parametrize("n", [2048, 2048 + 301, 1, 2049])
 @pytest.mark.parametrize("stat", ["skew", "kurt", "cv", "zscore"])
 def test_schedule_parity_small(deep, stat, n):
     from oracle import stats as ost
