@@ -176,6 +176,21 @@ class Plan(_Handle):
         return r
 
 
+_CONTEXTS = weakref.WeakSet()
+_ATEXIT = []
+
+
+def _close_all():
+    """Closes every open context before interpreter shutdown: a context returns
+    its device memory through the torch allocator callbacks, which must run
+    while torch is still alive."""
+    for c in list(_CONTEXTS):
+        try:
+            c.close()
+        except Exception:
+            pass
+
+
 class Context:
     """One parameter set on one GPU stream (not thread-safe)."""
 
@@ -209,6 +224,11 @@ class Context:
         if rc != 0:
             raise PpstError(rc, "ppst_ctx_create failed")
         self.ptr = out.value
+        _CONTEXTS.add(self)
+        if not _ATEXIT:  # registered after torch's own handlers, so it runs before them
+            import atexit
+            atexit.register(_close_all)
+            _ATEXIT.append(True)
         n = _lib.c_u32()
         lib.ppst_ctx_primes(self.ptr, None, 0, ctypes.byref(n))
         buf = np.zeros(n.value, dtype=np.uint64)

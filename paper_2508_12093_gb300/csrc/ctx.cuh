@@ -244,6 +244,9 @@ void ntt_inv(Ctx &c, const LimbMap &m);
 void ntt_inv_mul(Ctx &c, const LimbMap &m, const Tw *outmul);
 // the last (COLS) pass only, for limbs whose CHUNKS pass ran fused into another kernel
 void ntt_inv_cols_mul(Ctx &c, const LimbMap &m, const Tw *outmul);
+// rescale of a (level l) into out given limb l of both polynomials in the coefficient
+// domain (top, [2][N]) and per-limb multipliers mq_i (m_i q_l^-1); z: scratch [2][L+1][N]
+void ks_rescale(Ctx &c, const CtObj &a, const uint64_t *top, uint64_t *z, const ConstVec &mq, CtObj &out);
 LimbMap map_ct(const Ctx &c, uint64_t *d, int level);  // both polys of a ciphertext buffer
 LimbMap map_poly(const Ctx &c, uint64_t *d, int level); // one poly, limbs 0..level
 

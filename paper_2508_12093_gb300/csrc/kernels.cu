@@ -299,39 +299,6 @@ void k_moddown(Ctx &c, uint64_t *acc, int level, const uint64_t *add0, const uin
 // ---------------------------------------------------------------------------
 // rescale: c_i <- (c_i - [c_l]_centred) q_l^-1 mod q_i
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(EW_THREADS) k_rescale_bcast_kernel(const uint64_t *__restrict__ top,
-                                                                     uint64_t *__restrict__ w,
-                                                                     const PrimeC *__restrict__ pc, ConstVec qmod,
-                                                                     int N, int level, size_t wstride)
-{
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
-    const int row = blockIdx.y, k = row / level, i = row - k * level;
-    const uint64_t ql = pc[level].q;
-    const uint64_t v = top[(size_t)k * N + c];
-    const PrimeC p = pc[i];
-    uint64_t r = csub(shoup(v, 1, p.w64, p.q), p.q);  // v mod q_i
-    if (v > (ql >> 1)) r = sub_mod(r, qmod.c[i], p.q);  // centred: v - q_l
-    w[(size_t)k * wstride + (size_t)i * N + c] = r;
-}
-
-// out_i = (c_i m_i - w_i) q_l^-1 = c_i (m_i q_l^-1) - w_i q_l^-1 (m_i = 1 for a plain rescale)
-__global__ void __launch_bounds__(EW_THREADS) k_rescale_final_kernel(const uint64_t *__restrict__ a,
-                                                                     const uint64_t *__restrict__ w,
-                                                                     uint64_t *__restrict__ out,
-                                                                     const PrimeC *__restrict__ pc, ConstVec qlinv,
-                                                                     ConstVec mq, int N, int nl, size_t pstride)
-{
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
-    const int row = blockIdx.y, k = row / nl, i = row - k * nl;
-    const uint64_t q = pc[i].q;
-    const size_t o = (size_t)k * pstride + (size_t)i * N + c;
-    const uint64_t x = csub(shoup(a[o], mq.c[i], mq.sh[i], q), q);
-    const uint64_t y = csub(shoup(w[o], qlinv.c[i], qlinv.sh[i], q), q);
-    out[o] = sub_mod(x, y, q);
-}
-
 // top limb of both polynomials, times m (Shoup), into a scratch pair of rows
 __global__ void __launch_bounds__(EW_THREADS) k_top_copy_kernel(const uint64_t *__restrict__ a,
                                                                 uint64_t *__restrict__ top, uint64_t q, uint64_t m,
@@ -360,24 +327,14 @@ void k_rescale_mul(Ctx &c, const CtObj &a, const ConstVec *mul, CtObj &out)
     }
     LimbMap mt{top, (size_t)c.N, 1, 2, 1, l, 0};
     ntt_inv(c, mt);
-    {
-        ProfScope _ps(c, "rescale_bcast", (uint64_t)2 + 2 * l);
-        k_rescale_bcast_kernel<<<ew_grid(c, 2 * l), EW_THREADS, 0, c.stream>>>(top, c.ws_conv, c.d_pc,
-                                                                                c.resc_qmodv[l], c.N, l, ps);
-        check_launch("k_rescale_bcast");
-    }
-    LimbMap mw{c.ws_conv, ps, l, 2, l, 0, 0};
-    ntt_fwd(c, mw);
     ConstVec mq;
     for (int i = 0; i < l; i++) {
         const uint64_t qi = c.primes[i];
         mq.c[i] = mul ? h_mulmod(mul->c[i], c.resc[l].c[i], qi) : c.resc[l].c[i];
         mq.sh[i] = h_shoup(mq.c[i], qi);
     }
-    ProfScope _ps(c, "rescale_final", (uint64_t)6 * l);
-    k_rescale_final_kernel<<<ew_grid(c, 2 * l), EW_THREADS, 0, c.stream>>>(a.d, c.ws_conv, out.d, c.d_pc, c.resc[l],
-                                                                            mq, c.N, l, ps);
-    check_launch("k_rescale_final");
+    // the forward transform of [top]_centred mod q_i fused with its broadcast and the combine
+    ks_rescale(c, a, top, c.ws_conv, mq, out);
 }
 
 void k_rescale(Ctx &c, const CtObj &a, CtObj &out) { k_rescale_mul(c, a, nullptr, out); }

@@ -493,6 +493,128 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
 // ---------------------------------------------------------------------------
 static dim3 grid_s(const Ctx &c, int S, int rows) { return dim3((c.N >> S) / 16, rows); }
 
+// ---------------------------------------------------------------------------
+// rescale after Mul(P) (Sec. 3.1 levels): out_i = c_i m_i q_l^-1 - NTT([c_l]_centred mod q_i) q_l^-1
+// ---------------------------------------------------------------------------
+// COLS pass of [top]_centred mod q_i (top = limb l in the coefficient domain, L2-resident)
+template <int S>
+__global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
+    k_resc_cols(const uint64_t *__restrict__ top, uint64_t *__restrict__ z, const PrimeC *__restrict__ pc,
+                ConstVec qmod, const Tw *__restrict__ tw, int logN, int level, size_t z_stride)
+{
+    typedef PassShape<S> P;
+    __shared__ uint64_t sm[P::SMEM_WORDS];
+    const int N = 1 << logN, C = N >> S;
+    const int k = blockIdx.y / level, i = blockIdx.y - k * level;
+    const PrimeC p = pc[i];
+    const uint64_t ql = pc[level].q;
+    int h, sub;
+    pass_coords<S, true>(h, sub);
+    const int g = blockIdx.x * P::SUB + sub;
+    const uint64_t *tk = top + (size_t)k * N + g;
+    uint64_t x[P::E];
+#pragma unroll
+    for (int kk = 0; kk < P::E; kk++) {
+        const uint64_t v = tk[(size_t)(h + P::T * kk) * C];
+        uint64_t r = csub(shoup(v, 1, p.w64, p.q), p.q);  // v mod q_i
+        if (v > (ql >> 1)) r = sub_mod(r, qmod.c[i], p.q);  // centred: v - q_l
+        x[kk] = r;
+    }
+    cols_fwd_core<S>(x, sm, h, sub, tw + (size_t)i * N, p.q);
+    uint64_t *out = z + (size_t)k * z_stride + (size_t)i * N;
+#pragma unroll
+    for (int kk = 0; kk < P::E; kk++) out[(size_t)(P::E * h + kk) * C + g] = x[kk];
+}
+
+// CHUNKS pass of z and the combine; the block's tile of c is fetched by a bulk
+// asynchronous copy while z is transformed
+template <int S>
+struct RescSmem {
+    typedef PassShape<S> P;
+    static constexpr int TILE = P::SUB * P::M;
+    static constexpr size_t A_OFF = 128;
+    static constexpr size_t T_OFF = A_OFF + (size_t)TILE * 8;
+    static constexpr size_t BYTES = T_OFF + (size_t)P::SMEM_WORDS * 8;
+};
+
+template <int S>
+__global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
+    k_resc_chunks(const uint64_t *__restrict__ z, const uint64_t *__restrict__ a, uint64_t *__restrict__ out,
+                  const PrimeC *__restrict__ pc, ConstVec qlinv, ConstVec mq, const Tw *__restrict__ tw, int logN,
+                  int level, size_t z_stride, size_t pstride, int *err)
+{
+    typedef PassShape<S> P;
+    typedef RescSmem<S> SM;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    const uint64_t *at = reinterpret_cast<const uint64_t *>(smem + SM::A_OFF);
+    uint64_t *sm = reinterpret_cast<uint64_t *>(smem + SM::T_OFF);
+    const int N = 1 << logN;
+    const int k = blockIdx.y / level, i = blockIdx.y - k * level;
+    const uint64_t q = pc[i].q;
+    const size_t t0 = (size_t)i * N + (size_t)blockIdx.x * SM::TILE;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_fence_init();
+        mbar_arrive_expect_tx(&bar[0], SM::TILE * 8);
+        bulk_g2s(smem + SM::A_OFF, a + (size_t)k * pstride + t0, SM::TILE * 8, &bar[0]);
+    }
+    __syncthreads();
+    int h, sub;
+    pass_coords<S, false>(h, sub);
+    const int g = blockIdx.x * P::SUB + sub;
+    const int w0 = sub * P::M + h;
+    uint64_t x[P::E];
+    const uint64_t *src = z + (size_t)k * z_stride + t0 + w0;
+#pragma unroll
+    for (int kk = 0; kk < P::E; kk++) x[kk] = src[P::T * kk];
+    chunks_fwd_core<S>(x, sm, h, sub, g, N, tw + (size_t)i * N, q);
+    if (__syncthreads_or(!mbar_wait(&bar[0], 0))) {  // the tile did not arrive in time
+        if (threadIdx.x == 0) {
+            *(volatile int *)err = 1;
+            mbar_wait(&bar[0], 0);
+        }
+        return;
+    }
+    uint64_t *od = out + (size_t)k * pstride + t0 + w0;
+#pragma unroll
+    for (int kk = 0; kk < P::E; kk++) {
+        const uint64_t Z = reduce4q(x[kk], q);
+        const uint64_t xv = csub(shoup(at[w0 + P::T * kk], mq.c[i], mq.sh[i], q), q);
+        const uint64_t yv = csub(shoup(Z, qlinv.c[i], qlinv.sh[i], q), q);
+        od[P::T * kk] = sub_mod(xv, yv, q);
+    }
+}
+
+// top: limb l of both polynomials in the coefficient domain ([2][N]); z: scratch [2][L+1][N]
+void ks_rescale(Ctx &c, const CtObj &a, const uint64_t *top, uint64_t *z, const ConstVec &mq, CtObj &out)
+{
+    const int l = a.level;
+    const size_t ps = (size_t)(c.L + 1) * c.N;
+    {
+        ProfScope _ps(c, "rescale_cols", (uint64_t)2 * l + 2);
+        dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
+            constexpr int S = decltype(sv)::value;
+            k_resc_cols<S><<<grid_s(c, S, 2 * l), PassShape<S>::THREADS, 0, c.stream>>>(
+                top, z, c.d_pc, c.resc_qmodv[l], c.d_twf, c.logN, l, ps);
+        });
+        check_launch("k_resc_cols");
+    }
+    ProfScope _ps(c, "rescale_chunks", (uint64_t)6 * l);
+    dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
+        constexpr int S = decltype(sv)::value;
+        const size_t smem = RescSmem<S>::BYTES;
+        static std::atomic<bool> attr_set{false};
+        if (!attr_set.load()) {
+            PPST_CUDA(cudaFuncSetAttribute(k_resc_chunks<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr_set = true;
+        }
+        k_resc_chunks<S><<<grid_s(c, S, 2 * l), PassShape<S>::THREADS, smem, c.stream>>>(
+            z, a.d, out.d, c.d_pc, c.resc[l], mq, c.d_twf, c.logN, l, ps, ps, c.d_err);
+    });
+    check_launch("k_resc_chunks");
+}
+
 // stages 1-3 for B items: d (limbs 0..level) of item b in the evaluation domain
 // in ws_d2n[b] and (to be transformed) in ws_d2[b]; accumulators to ws_acc[b]
 // d2 (every item) has been through the first inverse pass (k_tensor_ic / k_automorph_ic)
