@@ -358,19 +358,20 @@ __global__ void __launch_bounds__(EW_THREADS) k_lincomb_kernel(LinArgs args, uin
         rs[threadIdx.x] = (uint64_t)(((u128)rr << 64) / q);
     }
     __syncthreads();
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
-    const size_t o = (size_t)poly * pstride + (size_t)i * N + c;
-    uint64_t acc = 0;
-    for (int k = 0; k < args.n; k++) acc = add_mod(acc, csub(shoup(args.p[k][o], r[k], rs[k], q), q), q);
-    out[o] = acc;
+    // grid-stride over the row: the weights' residues above are computed once per block
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const size_t o = (size_t)poly * pstride + (size_t)i * N + c;
+        uint64_t acc = 0;
+        for (int k = 0; k < args.n; k++) acc = add_mod(acc, csub(shoup(args.p[k][o], r[k], rs[k], q), q), q);
+        out[o] = acc;
+    }
 }
 
 void k_lincomb(Ctx &c, const LinArgs &args, int level, CtObj &out)
 {
     ProfScope _ps(c, "lincomb", (uint64_t)(args.n + 1) * 2 * (level + 1));
-    k_lincomb_kernel<<<ew_grid(c, 2 * (level + 1)), EW_THREADS, 0, c.stream>>>(args, out.d, c.d_pc, c.N, level + 1,
-                                                                                (size_t)(c.L + 1) * c.N);
+    const dim3 grid(std::max(1, c.N / (EW_THREADS * 8)), 2 * (level + 1));  // 8 words per thread
+    k_lincomb_kernel<<<grid, EW_THREADS, 0, c.stream>>>(args, out.d, c.d_pc, c.N, level + 1, (size_t)(c.L + 1) * c.N);
     check_launch("k_lincomb");
 }
 

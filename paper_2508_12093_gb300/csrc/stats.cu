@@ -161,8 +161,9 @@ struct Sched {
         cv_sched.notify_one();
     }
 
-    // ---- values shared by the queries in flight: a column's rotate-and-sum
-    // and its variance for a given B are computed by the first query that needs
+    // ---- values shared by the queries in flight: a column's rotate-and-sum,
+    // its variance for a given B and that variance's inverse square root for
+    // given approximation settings are computed by the first query that needs
     // them and reused by the others (the same ops on the same inputs: results
     // are bit-identical to a query run alone) ----
     struct Shared {
@@ -680,6 +681,14 @@ H col_var(Ev &ev, const Col &x, size_t n, double B, const H &R, const void *kx)
     return ev.shared_value(kx, 1, B, [&] { return variance(ev, x, n, B, R); });
 }
 
+// CryptoInvSqrt(Variance(x, B), B^2) (Sec. 5, Eq. 3): 1 / sqrt(Var), shared per column,
+// B and approximation settings (Z-score, skewness, kurtosis and PCC all start from it)
+H col_inv_sd(Ev &ev, const Col &x, size_t n, double B, const H &R, const void *kx, int k, int t)
+{
+    return ev.shared_value(kx, 2 | (k << 8) | (t << 16), B,
+                           [&] { return crypto_inv_sqrt(ev, col_var(ev, x, n, B, R, kx), B * B, k, t); });
+}
+
 H centred_power_sum(Ev &ev, const Col &x, const H &mu, int power)
 {
     const Col x1 = ev.sub_v(x, mu);
@@ -691,7 +700,7 @@ Col znorm(Ev &ev, const Col &x, size_t n, double B, int k, int t, const void *kx
 {
     H R = col_rsum(ev, x, kx);
     H mu = ev.mul_const(R, 1.0 / (double)n);
-    H inv = crypto_inv_sqrt(ev, col_var(ev, x, n, B, R, kx), B * B, k, t);
+    H inv = col_inv_sd(ev, x, n, B, R, kx, k, t);
     return ev.hmult_v(ev.sub_v(x, mu), Col{inv});
 }
 
@@ -706,7 +715,7 @@ H kurt(Ev &ev, const Col &x, size_t n, double B, int k, int t, const void *kx)
         X = ev.sub(X, ev.mul_int(ev.hmult(mu2, mu2), pads));
     }
     H num = ev.mul_const(X, 1.0 / (double)n);
-    H inv = crypto_inv_sqrt(ev, col_var(ev, x, n, B, R, kx), B * B, k, t);
+    H inv = col_inv_sd(ev, x, n, B, R, kx, k, t);
     H inv2 = ev.hmult(inv, inv);
     return ev.hmult(num, ev.hmult(inv2, inv2));
 }
@@ -722,7 +731,7 @@ H skew(Ev &ev, const Col &x, size_t n, double B, int k, int t, const void *kx)
         X = ev.add(X, ev.mul_int(ev.hmult(mu2, mu), pads));
     }
     H num = ev.mul_const(X, 1.0 / (double)n);
-    H inv = crypto_inv_sqrt(ev, col_var(ev, x, n, B, R, kx), B * B, k, t);
+    H inv = col_inv_sd(ev, x, n, B, R, kx, k, t);
     H inv3 = ev.hmult(ev.hmult(inv, inv), inv);
     return ev.hmult(num, inv3);
 }
@@ -748,8 +757,8 @@ H pcc(Ev &ev, const Col &x, const Col &y, size_t n, double Bx, double By, int k,
     const int64_t pads = (int64_t)(x.size() * (size_t)ev.c.S) - (int64_t)n;
     if (pads) Cs = ev.sub(Cs, ev.mul_int(ev.hmult(mux, muy), pads));
     H cov = ev.mul_const(Cs, 1.0 / (double)n);
-    H ix = crypto_inv_sqrt(ev, col_var(ev, x, n, Bx, Rx, kx), Bx * Bx, k, t);
-    H iy = crypto_inv_sqrt(ev, col_var(ev, y, n, By, Ry, ky), By * By, k, t);
+    H ix = col_inv_sd(ev, x, n, Bx, Rx, kx, k, t);
+    H iy = col_inv_sd(ev, y, n, By, Ry, ky, k, t);
     return ev.hmult(ev.hmult(cov, ix), iy);
 }
 
