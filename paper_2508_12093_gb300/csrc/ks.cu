@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
 // ---------------------------------------------------------------------------
 // 3. CHUNKS pass fused with the key inner product
 // ---------------------------------------------------------------------------
-// A block owns SUB consecutive chunks (one contiguous tile of SUB M words) of
+// A block owns 8 consecutive chunks (one contiguous tile of 8 M words) of
 // target limb e and loops over the digits. The digit tiles and the two key
 // tiles of a digit are brought into shared memory by bulk asynchronous copies:
 // digit j + 2 and the keys of digit j + 1 are in flight while digit j is
@@ -228,15 +228,17 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
 template <int S>
 struct InnerSmem {
     typedef PassShape<S> P;
-    static constexpr int TILE = P::SUB * P::M;  // words per tile
-    static constexpr size_t X_OFF = 128;        // after the barriers: two digit tiles
+    static constexpr int SUB = 8;                // chunks per block (two blocks per SM)
+    static constexpr int THREADS = SUB * P::T;
+    static constexpr int TILE = SUB * P::M;      // words per tile
+    static constexpr size_t X_OFF = 128;         // after the barriers: two digit tiles
     static constexpr size_t K_OFF = X_OFF + 2 * (size_t)TILE * 8;  // two key tiles
     static constexpr size_t T_OFF = K_OFF + 2 * (size_t)TILE * 8;  // transpose buffer
-    static constexpr size_t BYTES = T_OFF + (size_t)P::SMEM_WORDS * 8;
+    static constexpr size_t BYTES = T_OFF + (size_t)SUB * (P::M + P::M / P::E) * 8;
 };
 
 template <int S>
-__global__ void __launch_bounds__(PassShape<S>::THREADS, 1)
+__global__ void __launch_bounds__(InnerSmem<S>::THREADS, 2)
     k_inner_chunks(const uint64_t *__restrict__ ext, const uint64_t *__restrict__ d2n, const uint64_t *__restrict__ key,
                    uint64_t *__restrict__ acc, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN,
                    int level, int alpha, int L, int K, int nd, size_t ext_stride, int B, Ws ws, int *err)
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 1)
     __syncthreads();
     int h, sub;
     pass_coords<S, false>(h, sub);
-    const int g = tile * P::SUB + sub;
+    const int g = tile * SM::SUB + sub;
     const int w0 = sub * P::M + h;  // this thread's words of a tile: w0 + T k
     uint64_t a0[P::E], a1[P::E];
 #pragma unroll
@@ -647,14 +649,14 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
     ProfScope _ps(c, "inner_chunks", (uint64_t)E_ext * 2 * nd + (uint64_t)B * E_ext * (nd + 2));
     dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
-        const dim3 grid(B * ((c.N >> S) / PassShape<S>::SUB), E_ext);
+        const dim3 grid(B * ((c.N >> S) / InnerSmem<S>::SUB), E_ext);
         const size_t smem = InnerSmem<S>::BYTES;
         static std::atomic<bool> attr_set{false};
         if (!attr_set.load()) {
             PPST_CUDA(cudaFuncSetAttribute(k_inner_chunks<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr_set = true;
         }
-        k_inner_chunks<S><<<grid, PassShape<S>::THREADS, smem, c.stream>>>(
+        k_inner_chunks<S><<<grid, InnerSmem<S>::THREADS, smem, c.stream>>>(
             c.ws_ext, c.ws_d2n, key.d, c.ws_acc, c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, B, ws,
             c.d_err);
     });
