@@ -16,13 +16,13 @@
 
 namespace ppst {
 
-template <int S>
+template <int S, int SUB_ = 16>
 struct PassShape {
     static constexpr int M = 1 << S;
     static constexpr int A = (S + 1) / 2;  // register stages of round 1
     static constexpr int E = 1 << A;       // words per thread
     static constexpr int T = M / E;        // threads per sub-transform
-    static constexpr int SUB = 16;         // sub-transforms per block
+    static constexpr int SUB = SUB_;       // sub-transforms per block
     static constexpr int THREADS = SUB * T;
     static constexpr int SMEM_WORDS = SUB * (M + M / E);  // padded transpose buffer
     static constexpr int MIN_BLOCKS = THREADS >= 256 ? 3 : 4;
@@ -81,10 +81,10 @@ __host__ __device__ __forceinline__ uint32_t eval_address(uint32_t n, int logN)
 }
 
 // thread coordinates of a pass: COLS -> (sub = column in block, h), CHUNKS -> (h, sub = chunk in block)
-template <int S, bool COLS>
+template <int S, bool COLS, int SUB = 16>
 __device__ __forceinline__ void pass_coords(int &h, int &sub)
 {
-    typedef PassShape<S> P;
+    typedef PassShape<S, SUB> P;
     if (COLS) {
         sub = threadIdx.x % P::SUB;
         h = threadIdx.x / P::SUB;
@@ -95,11 +95,11 @@ __device__ __forceinline__ void pass_coords(int &h, int &sub)
 }
 
 // ---- forward, COLS pass: stages with m = 1 .. M/2 (distances in rows) ----
-template <int S>
+template <int S, int SUB = 16>
 __device__ __forceinline__ void cols_fwd_core(uint64_t (&x)[PassShape<S>::E], uint64_t *sm, int h, int sub,
                                               const Tw *__restrict__ T, uint64_t q)
 {
-    typedef PassShape<S> P;
+    typedef PassShape<S, SUB> P;
     const uint64_t q2 = 2 * q;
 #pragma unroll
     for (int s = P::A - 1; s >= 0; s--) {
@@ -209,11 +209,11 @@ __device__ __forceinline__ void chunks_inv_core(uint64_t (&x)[PassShape<S>::E], 
 }
 
 // ---- inverse, COLS pass (last inverse pass): rows E h + k in, h + T k out ----
-template <int S>
+template <int S, int SUB = 16>
 __device__ __forceinline__ void cols_inv_core(uint64_t (&x)[PassShape<S>::E], uint64_t *sm, int h, int sub,
                                               const Tw *__restrict__ T, uint64_t q)
 {
-    typedef PassShape<S> P;
+    typedef PassShape<S, SUB> P;
     const uint64_t q2 = 2 * q;
 #pragma unroll
     for (int d = 1; d <= P::T / 2; d <<= 1) {
