@@ -40,10 +40,12 @@ WORKLOAD = ("N=2^16 (32768 slots), 24 Q primes (60+23x50 bit) + 4 special 60-bit
 # (2 x 2 x 24 limbs), the relinearisation key (6 x 2 x 28 limbs) and the output
 # (2 x 24 limbs) of 2^16 words each
 HMULT_BYTES = (2 * 2 * 24 + 6 * 2 * 28 + 2 * 24) * 65536 * 8
-# DRAM bytes per algorithmic byte of a kernel, from one ncu capture of a
-# single-item top-level HMult (python -m paper_2508_12093_gb300.profcase hmult):
-# k_inner_chunks read 293.6 MB and wrote 21.7 MB against 293.6 MB algorithmic
-DRAM_PER_ALG = {"inner_chunks": (293.6 + 21.7) / 293.6}
+# DRAM bytes per algorithmic byte of a kernel, from ncu captures: k_inner_chunks
+# in a single-item top-level HMult (python -m paper_2508_12093_gb300.profcase hmult)
+# read 294.1 MB and wrote 20.8 MB against 293.6 MB algorithmic (1.073); with three
+# items (profcase batch3) 541.2 MB against 528.5 MB (1.024). The single-item
+# ratio is used: the larger of the two
+DRAM_PER_ALG = {"inner_chunks": (294.1 + 20.8) / 293.6}
 
 
 def peaks():
@@ -468,8 +470,9 @@ def main():
             "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if achieved else None,
                          "traffic": (DRAM_PER_ALG[dom] * alg_bytes / max(1, n_dom)) if dom in DRAM_PER_ALG else None,
-                         "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one single-item "
-                                            "top-level launch, scaled by the algorithmic bytes per launch"
+                         "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per algorithmic byte of "
+                                            "a single-item top-level launch (1.073; 1.024 with three items), times "
+                                            "the algorithmic bytes per launch"
                                             if dom in DRAM_PER_ALG else None),
                          "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback",

@@ -3,6 +3,7 @@
     python -m paper_2508_12093_gb300.profcase hmult      # N=2^16, 3 top-level HMult+KS
     python -m paper_2508_12093_gb300.profcase rotate     # N=2^16, 3 top-level rotations
     python -m paper_2508_12093_gb300.profcase query      # N=2^16, one kurtosis query
+    python -m paper_2508_12093_gb300.profcase batch3     # N=2^16, skew/kurt/CV of three columns, one batch
 
 Each case sets up keys and one ciphertext, runs a few warm-up iterations, then
 the profiled iterations, synchronises and prints "ok".
@@ -33,6 +34,14 @@ def main(case):
         sk, evk = ctx.keygen(2)
         col = ctx.encrypt_column(evk, workloads.lognormal_column(ctx.S, seed=1), 3)
         ctx.query(evk, "kurt", col, opts=dict(B_x=20.0, cheb_log2deg=7, newton_steps=3))
+    elif case == "batch3":
+        # three separately encrypted columns: every key switch of the batch runs on
+        # three items at one level (the first ones: the rotate-and-sums at level 23)
+        sk, evk = ctx.keygen(2)
+        x = workloads.lognormal_column(ctx.S, seed=1)
+        cols = [ctx.encrypt_column(evk, x, 3 + i) for i in range(3)]
+        opts = dict(B_x=20.0, cheb_log2deg=7, newton_steps=3)
+        ctx.query_batch(evk, [(s, c, None, opts) for s, c in zip(("skew", "kurt", "cv"), cols)])
     else:
         raise SystemExit(f"unknown case {case}")
     ctx.sync()
