@@ -22,6 +22,7 @@ template <int S>
 __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS)
     k_ntt_fwd_cols(LimbMap map, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN)
 {
+    pdl_begin();
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN, C = N >> S;
@@ -43,6 +44,7 @@ template <int S>
 __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS)
     k_ntt_fwd_chunks(LimbMap map, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN)
 {
+    pdl_begin();
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN;
@@ -65,6 +67,7 @@ template <int S>
 __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS)
     k_ntt_inv_chunks(LimbMap map, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN)
 {
+    pdl_begin();
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN;
@@ -89,6 +92,7 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCK
     k_ntt_inv_cols(LimbMap map, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN,
                    const Tw *__restrict__ outmul)
 {
+    pdl_begin();
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN, C = N >> S;
@@ -120,14 +124,14 @@ void ntt_fwd(Ctx &c, const LimbMap &m)
         ProfScope _ps(c, "ntt_cols_fwd", (uint64_t)2 * m.count());
         dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
             constexpr int S = decltype(sv)::value;
-            k_ntt_fwd_cols<S><<<pass_grid<S>(c, m), PassShape<S>::THREADS, 0, c.stream>>>(m, c.d_pc, c.d_twf, c.logN);
+            pdl_launch(c, k_ntt_fwd_cols<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twf, c.logN);
         });
         check_launch("ntt_cols_fwd");
     }
     ProfScope _ps(c, "ntt_chunks_fwd", (uint64_t)2 * m.count());
     dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
-        k_ntt_fwd_chunks<S><<<pass_grid<S>(c, m), PassShape<S>::THREADS, 0, c.stream>>>(m, c.d_pc, c.d_twf, c.logN);
+        pdl_launch(c, k_ntt_fwd_chunks<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twf, c.logN);
     });
     check_launch("ntt_chunks_fwd");
 }
@@ -139,7 +143,7 @@ void ntt_inv_mul(Ctx &c, const LimbMap &m, const Tw *outmul)
         ProfScope _ps(c, "ntt_chunks_inv", (uint64_t)2 * m.count());
         dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
             constexpr int S = decltype(sv)::value;
-            k_ntt_inv_chunks<S><<<pass_grid<S>(c, m), PassShape<S>::THREADS, 0, c.stream>>>(m, c.d_pc, c.d_twi,
+            pdl_launch(c, k_ntt_inv_chunks<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twi,
                                                                                              c.logN);
         });
         check_launch("ntt_chunks_inv");
@@ -153,7 +157,7 @@ void ntt_inv_cols_mul(Ctx &c, const LimbMap &m, const Tw *outmul)
     ProfScope _ps(c, "ntt_cols_inv", (uint64_t)2 * m.count());
     dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
-        k_ntt_inv_cols<S><<<pass_grid<S>(c, m), PassShape<S>::THREADS, 0, c.stream>>>(m, c.d_pc, c.d_twi, c.logN,
+        pdl_launch(c, k_ntt_inv_cols<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twi, c.logN,
                                                                                        outmul);
     });
     check_launch("ntt_cols_inv");
