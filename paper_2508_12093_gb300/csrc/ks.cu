@@ -607,7 +607,8 @@ void ks_rescale(Ctx &c, const CtObj &a, const uint64_t *top, uint64_t *z, const 
         ProfScope _ps(c, "rescale_cols", (uint64_t)2 * l + 2);
         dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
             constexpr int S = decltype(sv)::value;
-            pdl_launch(c, k_resc_cols<S>, grid_s(c, S, 2 * l), PassShape<S>::THREADS, 0, top, z, c.d_pc, c.resc_qmodv[l], c.d_twf, c.logN, l, ps);
+            pdl_launch(c, k_resc_cols<S>, grid_s(c, S, 2 * l), PassShape<S>::THREADS, 0, top, z, c.d_pc,
+                c.resc_qmodv[l], c.d_twf, c.logN, l, ps);
         });
         check_launch("k_resc_cols");
     }
@@ -620,7 +621,8 @@ void ks_rescale(Ctx &c, const CtObj &a, const uint64_t *top, uint64_t *z, const 
             PPST_CUDA(cudaFuncSetAttribute(k_resc_chunks<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr_set = true;
         }
-        pdl_launch(c, k_resc_chunks<S>, grid_s(c, S, 2 * l), PassShape<S>::THREADS, smem, z, a.d, out.d, c.d_pc, c.resc[l], mq, c.d_twf, c.logN, l, ps, ps, c.d_err);
+        pdl_launch(c, k_resc_chunks<S>, grid_s(c, S, 2 * l), PassShape<S>::THREADS, smem, z, a.d, out.d, c.d_pc,
+            c.resc[l], mq, c.d_twf, c.logN, l, ps, ps, c.d_err);
     });
     check_launch("k_resc_chunks");
 }
@@ -645,7 +647,8 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
             constexpr int S = decltype(sv)::value;
             dispatch_a(c.alpha, [&](auto av) {
                 constexpr int A = decltype(av)::value;
-                pdl_launch(c, k_modup_cols<S, A>, grid_s(c, S, B * nd * E_ext), PassShape<S>::THREADS, 0, c.ws_d2, c.ws_ext, c.d_ks, offs, c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, ws);
+                pdl_launch(c, k_modup_cols<S, A>, grid_s(c, S, B * nd * E_ext), PassShape<S>::THREADS, 0, c.ws_d2,
+                    c.ws_ext, c.d_ks, offs, c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, ws);
             });
         });
         check_launch("k_modup_cols");
@@ -663,8 +666,8 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
             PPST_CUDA(cudaFuncSetAttribute(k_inner_chunks<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr_set = true;
         }
-        pdl_launch(c, k_inner_chunks<S>, grid, InnerSmem<S>::THREADS, smem, c.ws_ext, c.ws_d2n, key.d, c.ws_acc, c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, B, ws,
-            c.d_err);
+        pdl_launch(c, k_inner_chunks<S>, grid, InnerSmem<S>::THREADS, smem, c.ws_ext, c.ws_d2n, key.d, c.ws_acc,
+            c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, B, ws, c.d_err);
     });
     check_launch("k_inner_chunks");
 }
@@ -708,8 +711,8 @@ static void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip)
             constexpr int S = decltype(sv)::value;
             dispatch_a(c.K, [&](auto kv) {
                 constexpr int KT = decltype(kv)::value;
-                pdl_launch(c, k_md_cols<S, RESC, KT>, grid_s(c, S, B * 2 * nl), PassShape<S>::THREADS, 0, c.ws_acc, c.ws_top, c.ws_conv, hMP, mdc, c.d_pc, c.d_twf, c.logN, level, nl, c.L, c.K, es, ps,
-                    ws);
+                pdl_launch(c, k_md_cols<S, RESC, KT>, grid_s(c, S, B * 2 * nl), PassShape<S>::THREADS, 0, c.ws_acc,
+                    c.ws_top, c.ws_conv, hMP, mdc, c.d_pc, c.d_twf, c.logN, level, nl, c.L, c.K, es, ps, ws);
             });
         });
         check_launch("k_md_cols");
@@ -724,7 +727,8 @@ static void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip)
                                            (int)smem));
             attr_set = true;
         }
-        pdl_launch(c, k_md_chunks<S, RESC>, grid_s(c, S, B * 2 * nl), PassShape<S>::THREADS, smem, c.ws_conv, c.ws_acc, ip, mdc, c.d_pc, c.d_twf, c.logN, nl, es, ps, ps, ws, c.d_err);
+        pdl_launch(c, k_md_chunks<S, RESC>, grid_s(c, S, B * 2 * nl), PassShape<S>::THREADS, smem, c.ws_conv,
+            c.ws_acc, ip, mdc, c.d_pc, c.d_twf, c.logN, nl, es, ps, ps, ws, c.d_err);
     });
     check_launch("k_md_chunks");
 }
@@ -757,7 +761,8 @@ std::vector<CtObj *> ev_hmult_batch(Ctx &c, const EvkObj &k, const std::vector<c
             ProfScope _ps(c, "tensor", (uint64_t)B * 7 * (lv + 1));
             dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
                 constexpr int S = decltype(sv)::value;
-                pdl_launch(c, k_tensor_ic<S>, dim3((c.N >> S) / PassShape<S>::SUB, B * (lv + 1)), PassShape<S>::THREADS, 0, ip, c.ws_d2, c.ws_d2n, c.d_pc, c.d_twi, c.logN, lv + 1, ps, ws.d2);
+                pdl_launch(c, k_tensor_ic<S>, dim3((c.N >> S) / PassShape<S>::SUB, B * (lv + 1)),
+                    PassShape<S>::THREADS, 0, ip, c.ws_d2, c.ws_d2n, c.d_pc, c.d_twi, c.logN, lv + 1, ps, ws.d2);
             });
             check_launch("k_tensor_ic");
         }
@@ -813,8 +818,9 @@ std::vector<CtObj *> ev_rotate_batch(Ctx &c, const EvkObj &k, const std::vector<
             ProfScope _ps(c, "automorph", (uint64_t)B * 5 * (lv + 1));
             dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
                 constexpr int S = decltype(sv)::value;
-                pdl_launch(c, k_automorph_ic<S>, dim3((c.N >> S) / PassShape<S>::SUB, B * 2 * (lv + 1)), PassShape<S>::THREADS, 0, ip, c.ws_d2, c.ws_d2n, c.d_pc, c.d_twi, c.logN, lv + 1,
-                                                   galois_elt(c, rr), ps, ws.d2);
+                pdl_launch(c, k_automorph_ic<S>, dim3((c.N >> S) / PassShape<S>::SUB, B * 2 * (lv + 1)),
+                    PassShape<S>::THREADS, 0, ip, c.ws_d2, c.ws_d2n, c.d_pc, c.d_twi, c.logN, lv + 1,
+                    galois_elt(c, rr), ps, ws.d2);
             });
             check_launch("k_automorph_ic");
         }

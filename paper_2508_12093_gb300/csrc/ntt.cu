@@ -124,7 +124,8 @@ void ntt_fwd(Ctx &c, const LimbMap &m)
         ProfScope _ps(c, "ntt_cols_fwd", (uint64_t)2 * m.count());
         dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
             constexpr int S = decltype(sv)::value;
-            pdl_launch(c, k_ntt_fwd_cols<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twf, c.logN);
+            pdl_launch(c, k_ntt_fwd_cols<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twf,
+                c.logN);
         });
         check_launch("ntt_cols_fwd");
     }
