@@ -122,6 +122,13 @@ int ppst_ctx_create(const ppst_params *params, const ppst_allocator *alloc, void
 const char *ppst_last_error(const ppst_ctx *ctx);
 /* primes_out[0 .. n_q + n_p) = q_0 .. q_L, p_0 .. p_{K-1}; *n_primes = n_q + n_p.
  * Writes at most `cap` primes. */
+/* Failure-detection self-test (no counterpart in the paper): launches one block
+ * that waits on a shared-memory barrier nothing completes, bounded by timeout_us
+ * (1 .. 10^6); like the kernels with asynchronous copies, it records the timeout
+ * in the context's error word and returns. The launch itself returns PPST_OK; the
+ * next synchronising call (ppst_sync, a decryption, an export) returns
+ * PPST_E_CUDA and clears the word; the context stays usable. */
+int ppst_selftest_wait(ppst_ctx *ctx, uint32_t timeout_us);
 int ppst_ctx_primes(const ppst_ctx *ctx, uint64_t *primes_out, size_t cap, uint32_t *n_primes);
 /* Block until all GPU work issued on the context's stream has finished. */
 int ppst_sync(ppst_ctx *ctx);

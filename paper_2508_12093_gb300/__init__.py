@@ -421,6 +421,11 @@ class Context:
     def drop(self, a, level):
         return self._new(lib.ppst_drop, a.ptr, level)
 
+    def selftest_wait(self, timeout_us):
+        """Launch a kernel whose bounded wait times out (failure-detection test);
+        the next synchronising call raises PpstError(PPST_E_CUDA)."""
+        self._check(lib.ppst_selftest_wait(self.ptr, int(timeout_us)))
+
     def sync(self):
         self._check(lib.ppst_sync(self.ptr))
 

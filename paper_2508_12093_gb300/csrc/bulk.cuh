@@ -61,13 +61,13 @@ __device__ __forceinline__ uint64_t global_ns()
 }
 
 // wait for the phase with the given parity to complete; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns = kWaitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t i = 0; i < kWaitIters; i++) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 255) == 255 && global_ns() - t0 > kWaitNs) return false;
+        if ((i & 255) == 255 && global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }

@@ -93,6 +93,16 @@ const char *ppst_last_error(const ppst_ctx *ctx)
     return c->err.msg.c_str();
 }
 
+int ppst_selftest_wait(ppst_ctx *ctx, uint32_t timeout_us)
+{
+    Ctx *c = (Ctx *)ctx;
+    if (!ok(c, TAG_CTX)) return PPST_E_ARG;
+    return guard(c, [&] {
+        REQ(timeout_us >= 1 && timeout_us <= 1000000, "timeout_us out of range [1, 10^6]");
+        wait_selftest(*c, timeout_us);
+    });
+}
+
 int ppst_ctx_primes(const ppst_ctx *ctx, uint64_t *primes_out, size_t cap, uint32_t *n_primes)
 {
     const Ctx *c = (const Ctx *)ctx;

@@ -328,6 +328,8 @@ CtObj *ev_inv_sqrt(Ctx &c, const EvkObj &k, const CtObj &v, double C, int cheb_l
 // PPST_E_CUDA if a kernel reported a timed-out wait (the word is then cleared);
 // call once the work in question has completed
 void check_device_error(Ctx &c);
+// launches one block whose bounded barrier wait runs out after timeout_us (ks.cu)
+void wait_selftest(Ctx &c, uint32_t timeout_us);
 
 // ---- serving and prepared queries (stats.cu) ----
 struct Server;

@@ -627,6 +627,30 @@ void ks_rescale(Ctx &c, const CtObj &a, const uint64_t *top, uint64_t *z, const 
     check_launch("k_resc_chunks");
 }
 
+// ---------------------------------------------------------------------------
+// failure-detection self-test: one block waits on a barrier whose phase never
+// completes (nothing is copied), gives up after limit_ns, records the timeout in
+// the error word and returns, exactly as the pipelined kernels do
+// ---------------------------------------------------------------------------
+__global__ void k_wait_selftest(int *err, uint64_t limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar[1];
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_fence_init();
+        mbar_arrive_expect_tx(&bar[0], 16);  // 16 bytes announced, none will arrive
+    }
+    __syncthreads();
+    if (__syncthreads_or(!mbar_wait(&bar[0], 0, limit_ns)))
+        if (threadIdx.x == 0) *(volatile int *)err = 1;
+}
+
+void wait_selftest(Ctx &c, uint32_t timeout_us)
+{
+    k_wait_selftest<<<1, 32, 0, c.stream>>>(c.d_err, (uint64_t)timeout_us * 1000);
+    check_launch("k_wait_selftest");
+}
+
 // stages 1-3 for B items: d (limbs 0..level) of item b in the evaluation domain
 // in ws_d2n[b] and (to be transformed) in ws_d2[b]; accumulators to ws_acc[b]
 // d2 (every item) has been through the first inverse pass (k_tensor_ic / k_automorph_ic)

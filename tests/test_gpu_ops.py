@@ -219,3 +219,21 @@ def test_every_digit_count(dnum):
     same(ctx, ctx.hmult(evk, ctx.drop(g, 6), g), oc.hmult(oc.drop(o, 6), o, ok))
     same(ctx, ctx.rotate(evk, g, 5), oc.rotate(o, 5, ok))
     assert np.abs(ctx.decrypt_ct(sk, ctx.rotate(evk, g, 5)) - np.roll(x, -5)).max() < 1e-6
+
+
+def test_bounded_wait_timeout_is_reported(env):
+    """A kernel whose barrier wait runs out (nothing is copied; the wait is bounded
+    by 20 ms) records the timeout in the error word and returns: the next
+    synchronising call reports PPST_E_CUDA once, and the context stays usable."""
+    import paper_2508_12093_gb300 as pp
+    ctx, sk, evk, oc, ok = env
+    ctx.selftest_wait(20000)
+    with pytest.raises(pp.PpstError) as e:
+        ctx.sync()
+    assert e.value.code == -6
+    ctx.sync()  # the word was cleared
+    _, oa, ga = fresh(env, 19)
+    same(ctx, ctx.hmult(evk, ga, ga), oc.hmult(oa, oa, ok))
+    with pytest.raises(pp.PpstError) as e:
+        ctx.selftest_wait(0)
+    assert e.value.code == -1
