@@ -168,6 +168,37 @@ def test_multi_ciphertext_column_full_size(big):
     assert np.abs(z - ref["znorm"]).max() / np.abs(ref["znorm"]).max() < TOL
 
 
+def test_million_row_columns_full_size(big):
+    """The largest columns of the served workload: 1,000,000 rows (31 ciphertexts,
+    ragged tail) for Z-score, CV and PCC, as one batch."""
+    from oracle import stats as ost
+    ctx, sk, evk = big
+    n = 1_000_000
+    x = workloads.lognormal_column(n, seed=4)
+    b, y = workloads.pcc_pair(n, seed=5)
+    cx, cb, cy = (ctx.encrypt_column(evk, v, 6 + i) for i, v in enumerate((x, b, y)))
+    res = ctx.query_batch(evk, [("zscore", cx, None, OPTS16), ("cv", cx, None, OPTS16),
+                                ("pcc", cb, cy, dict(OPTS16, B_x=1.0))])
+    ref = ost.plain_stats(x)
+    z, rep = ctx.decrypt(sk, res[0])
+    assert len(z) == n and rep["n_cts"] == 31
+    assert np.abs(z - ref["znorm"]).max() / np.abs(ref["znorm"]).max() < TOL
+    v, _ = ctx.decrypt(sk, res[1])
+    assert abs(v[0] / ref["cv"] - 1) < TOL
+    v, _ = ctx.decrypt(sk, res[2])
+    assert abs(v[0] / ost.plain_stats(b, y)["pcc"] - 1) < TOL
+
+
+def test_constant_column_runs(big):
+    """A constant column has variance 0, outside CryptoInvSqrt's domain (0, 2]: the
+    result is meaningless but the query completes (domain errors cannot be seen
+    on encrypted data)."""
+    ctx, sk, evk = big
+    col = ctx.encrypt_column(evk, np.full(5000, 3.0), 9)
+    v, rep = ctx.decrypt(sk, ctx.query(evk, "kurt", col, opts=OPTS16))
+    assert rep["depth_used"] == 19 and np.isfinite(v[0])
+
+
 def test_batch_full_size(big):
     """Twelve mixed queries over six columns of uneven lengths (the batched
     workload's shape) as one batch: every result identical to the query run
