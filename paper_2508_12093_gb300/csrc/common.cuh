@@ -36,18 +36,6 @@ struct __align__(16) Tw {
 
 __host__ __device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t q) { return x >= q ? x - q : x; }
 
-// Programmatic dependent launch (kernels launched with pdl_launch): pdl_begin()
-// waits until the previous kernel on the stream has completed and its writes are
-// visible, then lets the next kernel start launching; a kernel calls it before its
-// first global-memory access. Without the launch attribute both are no-ops.
-__device__ __forceinline__ void pdl_begin()
-{
-#ifdef __CUDA_ARCH__
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-#endif
-}
-
 __host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b)
 {
 #ifdef __CUDA_ARCH__

@@ -68,7 +68,6 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCK
     k_tensor_ic(ItemPtrs ip, uint64_t *__restrict__ d2, uint64_t *__restrict__ d2n, const PrimeC *__restrict__ pc,
                 const Tw *__restrict__ twi, int logN, int nl, size_t pstride, size_t d2_stride)
 {
-    pdl_begin();
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN;
@@ -105,7 +104,6 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCK
     k_automorph_ic(ItemPtrs ip, uint64_t *__restrict__ d2, uint64_t *__restrict__ d2n, const PrimeC *__restrict__ pc,
                    const Tw *__restrict__ twi, int logN, int nl, uint64_t gal, size_t pstride, size_t d2_stride)
 {
-    pdl_begin();
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN;
@@ -192,7 +190,6 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
                  DigitOffs offs, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN, int level,
                  int alpha, int L, int K, int nd, size_t ext_stride, Ws ws)
 {
-    pdl_begin();
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN, C = N >> S;
@@ -246,7 +243,6 @@ __global__ void __launch_bounds__(InnerSmem<S>::THREADS, 2)
                    uint64_t *__restrict__ acc, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN,
                    int level, int alpha, int L, int K, int nd, size_t ext_stride, int B, Ws ws, int *err)
 {
-    pdl_begin();
     typedef PassShape<S> P;
     typedef InnerSmem<S> SM;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -342,7 +338,6 @@ __global__ void __launch_bounds__(InnerSmem<S>::THREADS, 2)
 __global__ void k_md_top_kernel(ItemPtrs ip, uint64_t *__restrict__ acc, const PrimeC *__restrict__ pc, Tw pinv,
                                 int N, int level, size_t pstride, size_t ext_stride, Ws ws)
 {
-    pdl_begin();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     const int it = blockIdx.y / 2, k = blockIdx.y - 2 * it;
@@ -359,7 +354,6 @@ __global__ void k_md_topfix_kernel(const uint64_t *__restrict__ acc, uint64_t *_
                                    const uint64_t *__restrict__ hMP, const PrimeC *__restrict__ pc, Tw pinv, int N,
                                    int level, int L, int K, size_t ext_stride, Ws ws)
 {
-    pdl_begin();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     const int it = blockIdx.y / 2, k = blockIdx.y - 2 * it;
@@ -381,7 +375,6 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
               const Tw *__restrict__ tw, int logN, int level, int nl, int L, int K, size_t ext_stride,
               size_t z_stride, Ws ws)
 {
-    pdl_begin();
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN, C = N >> S;
@@ -438,7 +431,6 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
                 const MdC *__restrict__ mdc, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN, int nl,
                 size_t ext_stride, size_t z_stride, size_t pstride, Ws ws, int *err)
 {
-    pdl_begin();
     typedef PassShape<S> P;
     typedef MdSmem<S> SM;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -512,7 +504,6 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
     k_resc_cols(const uint64_t *__restrict__ top, uint64_t *__restrict__ z, const PrimeC *__restrict__ pc,
                 ConstVec qmod, const Tw *__restrict__ tw, int logN, int level, size_t z_stride)
 {
-    pdl_begin();
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN, C = N >> S;
@@ -554,7 +545,6 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
                   const PrimeC *__restrict__ pc, ConstVec qlinv, ConstVec mq, const Tw *__restrict__ tw, int logN,
                   int level, size_t z_stride, size_t pstride, int *err)
 {
-    pdl_begin();
     typedef PassShape<S> P;
     typedef RescSmem<S> SM;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -607,7 +597,7 @@ void ks_rescale(Ctx &c, const CtObj &a, const uint64_t *top, uint64_t *z, const 
         ProfScope _ps(c, "rescale_cols", (uint64_t)2 * l + 2);
         dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
             constexpr int S = decltype(sv)::value;
-            pdl_launch(c, k_resc_cols<S>, grid_s(c, S, 2 * l), PassShape<S>::THREADS, 0, top, z, c.d_pc,
+            launch_on(c, k_resc_cols<S>, grid_s(c, S, 2 * l), PassShape<S>::THREADS, 0, top, z, c.d_pc,
                 c.resc_qmodv[l], c.d_twf, c.logN, l, ps);
         });
         check_launch("k_resc_cols");
@@ -621,7 +611,7 @@ void ks_rescale(Ctx &c, const CtObj &a, const uint64_t *top, uint64_t *z, const 
             PPST_CUDA(cudaFuncSetAttribute(k_resc_chunks<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr_set = true;
         }
-        pdl_launch(c, k_resc_chunks<S>, grid_s(c, S, 2 * l), PassShape<S>::THREADS, smem, z, a.d, out.d, c.d_pc,
+        launch_on(c, k_resc_chunks<S>, grid_s(c, S, 2 * l), PassShape<S>::THREADS, smem, z, a.d, out.d, c.d_pc,
             c.resc[l], mq, c.d_twf, c.logN, l, ps, ps, c.d_err);
     });
     check_launch("k_resc_chunks");
@@ -671,7 +661,7 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
             constexpr int S = decltype(sv)::value;
             dispatch_a(c.alpha, [&](auto av) {
                 constexpr int A = decltype(av)::value;
-                pdl_launch(c, k_modup_cols<S, A>, grid_s(c, S, B * nd * E_ext), PassShape<S>::THREADS, 0, c.ws_d2,
+                launch_on(c, k_modup_cols<S, A>, grid_s(c, S, B * nd * E_ext), PassShape<S>::THREADS, 0, c.ws_d2,
                     c.ws_ext, c.d_ks, offs, c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, ws);
             });
         });
@@ -690,7 +680,7 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
             PPST_CUDA(cudaFuncSetAttribute(k_inner_chunks<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr_set = true;
         }
-        pdl_launch(c, k_inner_chunks<S>, grid, InnerSmem<S>::THREADS, smem, c.ws_ext, c.ws_d2n, key.d, c.ws_acc,
+        launch_on(c, k_inner_chunks<S>, grid, InnerSmem<S>::THREADS, smem, c.ws_ext, c.ws_d2n, key.d, c.ws_acc,
             c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, B, ws, c.d_err);
     });
     check_launch("k_inner_chunks");
@@ -710,7 +700,7 @@ static void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip)
     const dim3 eg(c.N / 256, 2 * B);
     if (RESC) {
         ProfScope _ps(c, "moddown_top", (uint64_t)6 * B);
-        pdl_launch(c, k_md_top_kernel, eg, 256, 0, ip, c.ws_acc, c.d_pc, hm.pinv, c.N, level, ps, es, ws);
+        launch_on(c, k_md_top_kernel, eg, 256, 0, ip, c.ws_acc, c.d_pc, hm.pinv, c.N, level, ps, es, ws);
         check_launch("k_md_top");
         // rows l .. l + K of both accumulators of every item (the top limb u_k, then
         // the P rows) to the coefficient domain in one transform: row l times N^-1,
@@ -725,7 +715,7 @@ static void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip)
     const uint64_t *hMP = c.d_ks + c.moddown_off + 2 * c.K;
     if (RESC) {
         ProfScope _ps(c, "moddown_top", (uint64_t)B * (2 * c.K + 4));
-        pdl_launch(c, k_md_topfix_kernel, eg, 256, 0, c.ws_acc, c.ws_top, hMP, c.d_pc, hm.pinv, c.N, level, c.L, c.K,
+        launch_on(c, k_md_topfix_kernel, eg, 256, 0, c.ws_acc, c.ws_top, hMP, c.d_pc, hm.pinv, c.N, level, c.L, c.K,
                                                       es, ws);
         check_launch("k_md_topfix");
     }
@@ -735,7 +725,7 @@ static void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip)
             constexpr int S = decltype(sv)::value;
             dispatch_a(c.K, [&](auto kv) {
                 constexpr int KT = decltype(kv)::value;
-                pdl_launch(c, k_md_cols<S, RESC, KT>, grid_s(c, S, B * 2 * nl), PassShape<S>::THREADS, 0, c.ws_acc,
+                launch_on(c, k_md_cols<S, RESC, KT>, grid_s(c, S, B * 2 * nl), PassShape<S>::THREADS, 0, c.ws_acc,
                     c.ws_top, c.ws_conv, hMP, mdc, c.d_pc, c.d_twf, c.logN, level, nl, c.L, c.K, es, ps, ws);
             });
         });
@@ -751,7 +741,7 @@ static void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip)
                                            (int)smem));
             attr_set = true;
         }
-        pdl_launch(c, k_md_chunks<S, RESC>, grid_s(c, S, B * 2 * nl), PassShape<S>::THREADS, smem, c.ws_conv,
+        launch_on(c, k_md_chunks<S, RESC>, grid_s(c, S, B * 2 * nl), PassShape<S>::THREADS, smem, c.ws_conv,
             c.ws_acc, ip, mdc, c.d_pc, c.d_twf, c.logN, nl, es, ps, ps, ws, c.d_err);
     });
     check_launch("k_md_chunks");
@@ -785,7 +775,7 @@ std::vector<CtObj *> ev_hmult_batch(Ctx &c, const EvkObj &k, const std::vector<c
             ProfScope _ps(c, "tensor", (uint64_t)B * 7 * (lv + 1));
             dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
                 constexpr int S = decltype(sv)::value;
-                pdl_launch(c, k_tensor_ic<S>, dim3((c.N >> S) / PassShape<S>::SUB, B * (lv + 1)),
+                launch_on(c, k_tensor_ic<S>, dim3((c.N >> S) / PassShape<S>::SUB, B * (lv + 1)),
                     PassShape<S>::THREADS, 0, ip, c.ws_d2, c.ws_d2n, c.d_pc, c.d_twi, c.logN, lv + 1, ps, ws.d2);
             });
             check_launch("k_tensor_ic");
@@ -842,7 +832,7 @@ std::vector<CtObj *> ev_rotate_batch(Ctx &c, const EvkObj &k, const std::vector<
             ProfScope _ps(c, "automorph", (uint64_t)B * 5 * (lv + 1));
             dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
                 constexpr int S = decltype(sv)::value;
-                pdl_launch(c, k_automorph_ic<S>, dim3((c.N >> S) / PassShape<S>::SUB, B * 2 * (lv + 1)),
+                launch_on(c, k_automorph_ic<S>, dim3((c.N >> S) / PassShape<S>::SUB, B * 2 * (lv + 1)),
                     PassShape<S>::THREADS, 0, ip, c.ws_d2, c.ws_d2n, c.d_pc, c.d_twi, c.logN, lv + 1,
                     galois_elt(c, rr), ps, ws.d2);
             });

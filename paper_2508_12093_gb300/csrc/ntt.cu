@@ -22,7 +22,6 @@ template <int S>
 __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS)
     k_ntt_fwd_cols(LimbMap map, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN)
 {
-    pdl_begin();
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN, C = N >> S;
@@ -44,7 +43,6 @@ template <int S>
 __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS)
     k_ntt_fwd_chunks(LimbMap map, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN)
 {
-    pdl_begin();
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN;
@@ -67,7 +65,6 @@ template <int S>
 __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS)
     k_ntt_inv_chunks(LimbMap map, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN)
 {
-    pdl_begin();
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN;
@@ -92,7 +89,6 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCK
     k_ntt_inv_cols(LimbMap map, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN,
                    const Tw *__restrict__ outmul)
 {
-    pdl_begin();
     typedef PassShape<S> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN, C = N >> S;
@@ -124,7 +120,7 @@ void ntt_fwd(Ctx &c, const LimbMap &m)
         ProfScope _ps(c, "ntt_cols_fwd", (uint64_t)2 * m.count());
         dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
             constexpr int S = decltype(sv)::value;
-            pdl_launch(c, k_ntt_fwd_cols<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twf,
+            launch_on(c, k_ntt_fwd_cols<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twf,
                 c.logN);
         });
         check_launch("ntt_cols_fwd");
@@ -132,7 +128,7 @@ void ntt_fwd(Ctx &c, const LimbMap &m)
     ProfScope _ps(c, "ntt_chunks_fwd", (uint64_t)2 * m.count());
     dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
-        pdl_launch(c, k_ntt_fwd_chunks<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twf, c.logN);
+        launch_on(c, k_ntt_fwd_chunks<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twf, c.logN);
     });
     check_launch("ntt_chunks_fwd");
 }
@@ -144,7 +140,7 @@ void ntt_inv_mul(Ctx &c, const LimbMap &m, const Tw *outmul)
         ProfScope _ps(c, "ntt_chunks_inv", (uint64_t)2 * m.count());
         dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
             constexpr int S = decltype(sv)::value;
-            pdl_launch(c, k_ntt_inv_chunks<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twi,
+            launch_on(c, k_ntt_inv_chunks<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twi,
                                                                                              c.logN);
         });
         check_launch("ntt_chunks_inv");
@@ -158,7 +154,7 @@ void ntt_inv_cols_mul(Ctx &c, const LimbMap &m, const Tw *outmul)
     ProfScope _ps(c, "ntt_cols_inv", (uint64_t)2 * m.count());
     dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
-        pdl_launch(c, k_ntt_inv_cols<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twi, c.logN,
+        launch_on(c, k_ntt_inv_cols<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twi, c.logN,
                                                                                        outmul);
     });
     check_launch("ntt_cols_inv");

@@ -17,23 +17,15 @@
 
 namespace ppst {
 
-// launch with programmatic stream serialization: the kernel may be scheduled
-// while the previous kernel on the stream drains (it calls pdl_begin() first).
-// Used from N = 2^15 up; below that the kernels are short enough that the extra
-// launch work costs more than the overlap gains (plain launches)
+// launch on the context's stream (configuration and arguments as for <<<...>>>)
 template <class... KArgs, class... Args>
-inline void pdl_launch(Ctx &c, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, Args &&...args)
+inline void launch_on(Ctx &c, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, Args &&...args)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = c.stream;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = c.logN >= 15 ? 1 : 0;
     PPST_CUDA(cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...));
 }
 

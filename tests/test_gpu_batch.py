@@ -74,3 +74,34 @@ def test_autotune_picks_a_measured_dnum(tmp_path):
     again, _ = autotune.tune(base, cache=cache, candidates=(2, 3, 6), reps=3, query=q)  # from the cache
     assert again == best
     assert autotune.tuned_params(base, cache=cache)["n_p"] == 12 // best
+
+
+def test_many_queries_deterministic_full_size():
+    """96 mixed queries of the 64-column workload at N = 2^16 with digits of 8
+    primes (dnum = 3), run one at a time and through the request loop (32 in
+    flight): every result identical in both forms and within 1e-3 of FP64. Guards
+    against ordering races between consecutive launches."""
+    import bench
+    import paper_2508_12093_gb300 as pp
+    from oracle import stats as ost
+    from paper_2508_12093_gb300 import autotune
+    ctx = pp.Context(autotune.with_dnum(workloads.PARAMS["n16_d6"], 3))
+    sk, evk = ctx.keygen(2)
+    cols, data = bench.batched_columns(ctx, evk)
+    qs = bench.batched_queries(cols)[:96]
+    serial = [ctx.query(evk, *q[:4]) for q in qs]
+    srv = pp.Server(ctx, evk, 48 << 30, 32)
+    ts = [srv.submit(*q[:4]) for q in qs]
+    served = [srv.wait(t) for t in ts]
+    srv.close()
+    for q, a, b in zip(qs, serial, served):
+        for x, y in zip(a.cts(), b.cts()):
+            x, y = ctx.ct_export(x), ctx.ct_export(y)
+            assert x[2:] == y[2:] and np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1]), (q[0], q[4])
+        vals, _ = ctx.decrypt(sk, b)
+        if q[0] == "pcc":
+            want = np.array([ost.plain_stats(data[q[4][0]], data[q[4][1]])["pcc"]])
+        else:
+            ref = ost.plain_stats(data[q[4][0]])
+            want = ref["znorm"] if q[0] == "zscore" else np.array([ref[q[0]]])
+        assert np.abs(vals[:len(want)] - want).max() / np.abs(want).max() < 1e-3, (q[0], q[4])

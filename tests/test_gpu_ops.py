@@ -200,14 +200,16 @@ def test_error_codes(env):
         assert e.value.code == -1
 
 
-@pytest.mark.parametrize("dnum", [1, 2, 3, 4, 6, 12])
-def test_every_digit_count(dnum):
+@pytest.mark.parametrize("n_q,dnum", [(12, 1), (12, 2), (12, 3), (12, 4), (12, 6), (12, 12), (24, 2), (24, 3),
+                                        (24, 4), (24, 6)])
+def test_every_digit_count(n_q, dnum):
     """Key switching for every decomposition of a 12-prime chain (digits of
-    12, 6, 4, 3, 2 and 1 primes, K = digit size): HMult at the top level and
+    12, 6, 4, 3, 2 and 1 primes, K = digit size) and of the 24-prime chain the
+    autotuner chooses from (digits of 12, 8, 6, 4): HMult at the top level and
     one level down, and a rotation, bit-exact against the oracle."""
     import paper_2508_12093_gb300 as pp
     from oracle import ckks as ock
-    prm = dict(log_n=12, n_q=12, n_p=12 // dnum, dnum=dnum, q0_bits=60, q_bits=40, p_bits=60, log_scale=40)
+    prm = dict(log_n=12, n_q=n_q, n_p=n_q // dnum, dnum=dnum, q0_bits=60, q_bits=40, p_bits=60, log_scale=40)
     ctx = pp.Context(prm)
     sk, evk = ctx.keygen(11, rotations=[5])
     oc = ock.Ckks(ock.Params(**prm))
