@@ -32,7 +32,7 @@ inline void launch_on(Ctx &c, void (*k)(KArgs...), dim3 grid, dim3 block, size_t
 template <int S, int SUB_ = 16>
 struct PassShape {
     static constexpr int M = 1 << S;
-    static constexpr int A = (S + 1) / 2;  // register stages of round 1
+    static constexpr int A = (S + 1) / 2;  // register stages before the transpose
     static constexpr int E = 1 << A;       // words per thread
     static constexpr int T = M / E;        // threads per sub-transform
     static constexpr int SUB = SUB_;       // sub-transforms per block

@@ -290,3 +290,35 @@ def test_znorm_on_ckks_cfg1_shape():
     got = c.decrypt(keys["s"], z)
     ref = stats.plain_stats(x)["znorm"]
     assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-3
+
+
+def test_symmetric_column_has_zero_skew():
+    """Data symmetric about its mean: the plain skewness is 0 and the simulated
+    schedule's numerator (the centred third-moment sum) vanishes, so the
+    encrypted skewness is 0 up to the approximation's absolute error."""
+    S = 1024
+    ev = sim_for(S=S, levels=24)
+    half = workloads.lognormal_column(500, seed=7)
+    x = np.concatenate([half, 2 * half.mean() - half])  # mirrored about the mean
+    assert abs(stats.plain_stats(x)["skew"]) < 1e-12
+    r = stats.skew(ev, [ev.encrypt(x)], len(x), 20.0, 7, 3)
+    assert abs(r.v[0]) < 1e-9
+
+
+def test_lognormal_moments_closed_form():
+    """Large-sample sanity check of the population moments against the closed
+    forms of lognormal(mu, sigma): skew = (e^s2 + 2) sqrt(e^s2 - 1), kurt =
+    e^(4 s2) + 2 e^(3 s2) + 3 e^(2 s2) - 3, CV = sqrt(e^s2 - 1)."""
+    s2 = 0.3 ** 2
+    x = np.random.default_rng(11).lognormal(1.0, 0.3, 4_000_000)
+    st = stats.plain_stats(x)
+    assert abs(st["skew"] / ((math.exp(s2) + 2) * math.sqrt(math.exp(s2) - 1)) - 1) < 0.02
+    assert abs(st["kurt"] / (math.exp(4 * s2) + 2 * math.exp(3 * s2) + 3 * math.exp(2 * s2) - 3) - 1) < 0.02
+    assert abs(st["cv"] / math.sqrt(math.exp(s2) - 1) - 1) < 0.005
+
+
+def test_constant_column_is_outside_the_domain():
+    """A constant column has variance 0: 1/sqrt(Var) is undefined (the FP64
+    reference flags it; on encrypted data it cannot be detected)."""
+    with pytest.raises(ZeroDivisionError):
+        stats.plain_stats(np.full(100, 3.0))
