@@ -310,15 +310,15 @@ def test_lognormal_moments_closed_form():
     forms of lognormal(mu, sigma): skew = (e^s2 + 2) sqrt(e^s2 - 1), kurt =
     e^(4 s2) + 2 e^(3 s2) + 3 e^(2 s2) - 3, CV = sqrt(e^s2 - 1)."""
     s2 = 0.3 ** 2
-    x = np.random.default_rng(11).lognormal(1.0, 0.3, 4_000_000)
+    x = np.random.default_rng(11).lognormal(1.0, 0.3, 1_000_000)
     st = stats.plain_stats(x)
-    assert abs(st["skew"] / ((math.exp(s2) + 2) * math.sqrt(math.exp(s2) - 1)) - 1) < 0.02
-    assert abs(st["kurt"] / (math.exp(4 * s2) + 2 * math.exp(3 * s2) + 3 * math.exp(2 * s2) - 3) - 1) < 0.02
+    assert abs(st["skew"] / ((math.exp(s2) + 2) * math.sqrt(math.exp(s2) - 1)) - 1) < 0.03
+    assert abs(st["kurt"] / (math.exp(4 * s2) + 2 * math.exp(3 * s2) + 3 * math.exp(2 * s2) - 3) - 1) < 0.03
     assert abs(st["cv"] / math.sqrt(math.exp(s2) - 1) - 1) < 0.005
 
 
 def test_constant_column_is_outside_the_domain():
     """A constant column has variance 0: 1/sqrt(Var) is undefined (the FP64
     reference flags it; on encrypted data it cannot be detected)."""
-    with pytest.raises(ZeroDivisionError):
+    with pytest.raises(ZeroDivisionError), np.errstate(divide="ignore", invalid="ignore"):
         stats.plain_stats(np.full(100, 3.0))
