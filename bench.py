@@ -460,7 +460,8 @@ def main():
             "inv_sqrt_sec72": sweep72,
             "toy12_zscore": toy,
             "batched64": b64,
-            "hmult_ks_by_dnum": ({str(r["dnum"]): {"us": r["hmult_us"], "algorithmic_bytes": r["algorithmic_bytes"],
+            "hmult_ks_by_dnum": ({str(r["dnum"]): {"us": r["hmult_us"], "tile": r["tile"], "us_by_tile": r["tile_us"],
+                                                   "algorithmic_bytes": r["algorithmic_bytes"],
                                                    "frac_of_hbm": r.get("hmult_frac_of_hbm"),
                                                    "rotate_us": r["rotate_us"], "skew_query_ms": r["query_us"] / 1e3}
                                   for r in b64["autotune"]} if b64 else None),
@@ -700,7 +701,9 @@ def batched64(pp, ost, params, peak):
     from paper_2508_12093_gb300 import autotune
     best, table = autotune.tune(params, cache=None, peak_gbs=peak)
     prm = autotune.with_dnum(params, best)
+    tile = next(r for r in table if r["dnum"] == best)["tile"]
     ctx = pp.Context(prm)
+    ctx.set_tile(tile)
     sk, evk = ctx.keygen(2)
     cols, data = batched_columns(ctx, evk)
     qs = batched_queries(cols)
@@ -732,12 +735,14 @@ def batched64(pp, ost, params, peak):
         worst = max(worst, float(np.abs(vals[:len(want)] - want).max() / np.abs(want).max()))
     ctx.close()
     return {"value": len(qs) / batch_s, "unit": "queries/s", "serial_value": len(qs) / serial_s,
-            "speedup_vs_serial": serial_s / batch_s, "queries": len(qs), "dnum": best, "gpu_launches": launches,
+            "speedup_vs_serial": serial_s / batch_s, "queries": len(qs), "dnum": best, "inner_tile": tile,
+            "gpu_launches": launches,
             "max_rel_err_vs_fp64": worst,
             "workload": (f"{BATCH_COLS} columns of log-uniform 1k-32k rows (one ciphertext each), in pairs of "
                          "y = (lognormal(9, 0.6) + 20000 b + N(0, 3000^2))/1000 and b ~ Bernoulli(0.2); Z-score, CV, skewness, kurtosis of every "
                          "column and Pearson correlation of every pair (B=20 lognormal, 1 Bernoulli), "
-                         "Chebyshev degree 127, 3 Newton steps, dnum autotuned over {3,4,6,12}"),
+                         "Chebyshev degree 127, 3 Newton steps, dnum autotuned over {3,4,6,12} and the inner-product "
+                         "tile over {4,8,16} chunks per block"),
             "autotune": table}
 
 

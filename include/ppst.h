@@ -122,6 +122,10 @@ int ppst_ctx_create(const ppst_params *params, const ppst_allocator *alloc, void
 const char *ppst_last_error(const ppst_ctx *ctx);
 /* primes_out[0 .. n_q + n_p) = q_0 .. q_L, p_0 .. p_{K-1}; *n_primes = n_q + n_p.
  * Writes at most `cap` primes. */
+/* Tile of the key-switching inner product (no counterpart in the paper): the
+ * transform chunks each block owns, 4, 8 (default) or 16 (PPST_E_ARG
+ * otherwise). Changes speed only, never results; the autotuner measures it. */
+int ppst_ctx_set_tile(ppst_ctx *ctx, uint32_t inner_sub);
 /* Failure-detection self-test (no counterpart in the paper): launches one block
  * that waits on a shared-memory barrier nothing completes, bounded by timeout_us
  * (1 .. 10^6); like the kernels with asynchronous copies, it records the timeout

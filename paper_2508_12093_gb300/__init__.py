@@ -421,6 +421,11 @@ class Context:
     def drop(self, a, level):
         return self._new(lib.ppst_drop, a.ptr, level)
 
+    def set_tile(self, inner_sub):
+        """Chunks per block of the key-switching inner product (4, 8 or 16)."""
+        self._check(lib.ppst_ctx_set_tile(self.ptr, int(inner_sub)))
+        self.inner_sub = int(inner_sub)
+
     def selftest_wait(self, timeout_us):
         """Launch a kernel whose bounded wait times out (failure-detection test);
         the next synchronising call raises PpstError(PPST_E_CUDA)."""

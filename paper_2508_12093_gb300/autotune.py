@@ -1,13 +1,16 @@
-"""Autotuner for the key-switching decomposition (dnum) of a parameter family.
+"""Autotuner for the key-switching decomposition (dnum) and the inner-product
+tile of a parameter family.
 
 Hybrid key switching splits the Q chain into dnum digits of alpha = n_q / dnum
 primes and extends each digit over K = alpha special primes. Fewer digits
 mean fewer ModUp transforms and a smaller evaluation key but a wider base
-conversion and a longer ModDown; which dnum is fastest is a property of the
-GPU, so it is measured: for every candidate the tuner builds a context with
-its own keys, times HMult + key switch and a rotation at the top level, and
-one representative statistic query, and picks the dnum with the fastest query.
-Results are cached in a JSON file keyed by device and parameters.
+conversion and a longer ModDown; the key inner product's blocks own 4, 8 or 16
+transform chunks (more chunks: longer blocks, fewer per SM). Which choice is
+fastest is a property of the GPU, so it is measured: for every dnum the tuner
+builds a context with its own keys, times top-level HMult + key switch for each
+tile, then a rotation and one representative statistic query with the best
+tile, and picks the dnum with the fastest query. Results are cached in a JSON
+file keyed by device and parameters.
 
     python -m paper_2508_12093_gb300.autotune [family] [--cache PATH]
 """
@@ -23,6 +26,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 CANDIDATES = (3, 4, 6, 12)
+TILES = (4, 8, 16)  # transform chunks per block of the key inner product
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuned.json")
 
 
@@ -61,8 +65,13 @@ def measure(params, reps=20, query=None, peak_gbs=None):
     ctx = pp.Context(params)
     sk, evk = ctx.keygen(2)  # relinearisation key and the Galois keys of rotations by 2^i
     a = ctx.encrypt_ints(evk, np.zeros(ctx.N, dtype=np.int64), 9, 0, 2.0 ** params["log_scale"])
-    out = {"dnum": params["dnum"], "n_p": params["n_p"]}
-    out["hmult_us"] = _timed(lambda: ctx.hmult(evk, a, a), reps)
+    out = {"dnum": params["dnum"], "n_p": params["n_p"], "tile_us": {}}
+    for tile in TILES:
+        ctx.set_tile(tile)
+        out["tile_us"][str(tile)] = _timed(lambda: ctx.hmult(evk, a, a), reps)
+    out["tile"] = int(min(out["tile_us"], key=out["tile_us"].get))
+    ctx.set_tile(out["tile"])
+    out["hmult_us"] = out["tile_us"][str(out["tile"])]
     out["rotate_us"] = _timed(lambda: ctx.rotate(evk, a, 1), reps)
     out["algorithmic_bytes"] = ks_bytes(params)
     out["hmult_gbs"] = out["algorithmic_bytes"] / (out["hmult_us"] * 1e-6) / 1e9
@@ -87,7 +96,8 @@ QUERY = ("skew", dict(B_x=20.0, cheb_log2deg=7, newton_steps=3))
 
 
 def tune(params, cache=DEFAULT_CACHE, candidates=CANDIDATES, reps=20, refresh=False, peak_gbs=None, query=QUERY):
-    """Returns (best dnum, table of measurements), from the cache when present."""
+    """Returns (best dnum, table of measurements), from the cache when present;
+    each table row holds the tile chosen for that dnum."""
     key = _key(params)
     db = {}
     if cache and os.path.exists(cache):
@@ -114,6 +124,14 @@ def tuned_params(params, cache=DEFAULT_CACHE, **kw):
     """params with the tuned dnum (and its K)."""
     best, _ = tune(params, cache=cache, **kw)
     return with_dnum(params, best)
+
+
+def tuned_setup(params, cache=DEFAULT_CACHE, **kw):
+    """(params with the tuned dnum, the inner-product tile measured best for it);
+    apply the tile with Context.set_tile."""
+    best, table = tune(params, cache=cache, **kw)
+    row = next(r for r in table if r["dnum"] == best)
+    return with_dnum(params, best), row["tile"]
 
 
 if __name__ == "__main__":

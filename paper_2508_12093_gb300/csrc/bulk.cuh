@@ -23,6 +23,14 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 // make the initialised barriers visible to the async proxy
 __device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
+// orders this thread's earlier generic-proxy accesses to shared memory (and, after
+// a barrier, the CTA's) before its following asynchronous-proxy operations: issued
+// before a bulk copy overwrites a buffer the CTA has been reading
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // one arrival that also announces `bytes` of transactions for the current phase
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
 {

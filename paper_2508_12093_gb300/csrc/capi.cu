@@ -93,6 +93,16 @@ const char *ppst_last_error(const ppst_ctx *ctx)
     return c->err.msg.c_str();
 }
 
+int ppst_ctx_set_tile(ppst_ctx *ctx, uint32_t inner_sub)
+{
+    Ctx *c = (Ctx *)ctx;
+    if (!ok(c, TAG_CTX)) return PPST_E_ARG;
+    return guard(c, [&] {
+        REQ(inner_sub == 4 || inner_sub == 8 || inner_sub == 16, "inner_sub must be 4, 8 or 16");
+        c->inner_sub = (int)inner_sub;
+    });
+}
+
 int ppst_selftest_wait(ppst_ctx *ctx, uint32_t timeout_us)
 {
     Ctx *c = (Ctx *)ctx;

@@ -175,6 +175,7 @@ struct Ctx {
     uint64_t *ws_top = nullptr;  // [2][N]
     int ws_items = 0;
     size_t ws_bytes = 0;
+    int inner_sub = 8;  // chunks per block of the key inner product (4, 8 or 16; autotuned)
 
     size_t ct_words() const { return (size_t)2 * (L + 1) * N; }
     size_t ext_rows() const { return (size_t)(L + 1 + K); }

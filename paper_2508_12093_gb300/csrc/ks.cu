@@ -220,15 +220,17 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
 // ---------------------------------------------------------------------------
 // 3. CHUNKS pass fused with the key inner product
 // ---------------------------------------------------------------------------
-// A block owns 8 consecutive chunks (one contiguous tile of 8 M words) of
-// target limb e and loops over the digits. The digit tiles and the two key
+// A block owns SUB consecutive chunks (one contiguous tile of SUB M words; SUB
+// = 4, 8 or 16, chosen per context by the autotuner, 8 by default) of target
+// limb e and loops over the digits. The digit tiles and the two key
 // tiles of a digit are brought into shared memory by bulk asynchronous copies:
 // digit j + 2 and the keys of digit j + 1 are in flight while digit j is
 // transformed and accumulated, so the HBM latency is off the critical path.
-template <int S>
+template <int S, int SUB_>
 struct InnerSmem {
     typedef PassShape<S> P;
-    static constexpr int SUB = 8;                // chunks per block (two blocks per SM)
+    static constexpr int SUB = SUB_;             // chunks per block
+    static constexpr int MIN_BLOCKS = 16 / SUB_; // blocks per SM the shared memory allows
     static constexpr int THREADS = SUB * P::T;
     static constexpr int TILE = SUB * P::M;      // words per tile
     static constexpr size_t X_OFF = 128;         // after the barriers: two digit tiles
@@ -237,14 +239,14 @@ struct InnerSmem {
     static constexpr size_t BYTES = T_OFF + (size_t)SUB * (P::M + P::M / P::E) * 8;
 };
 
-template <int S>
-__global__ void __launch_bounds__(InnerSmem<S>::THREADS, 2)
+template <int S, int SUB>
+__global__ void __launch_bounds__(InnerSmem<S, SUB>::THREADS, InnerSmem<S, SUB>::MIN_BLOCKS)
     k_inner_chunks(const uint64_t *__restrict__ ext, const uint64_t *__restrict__ d2n, const uint64_t *__restrict__ key,
                    uint64_t *__restrict__ acc, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN,
                    int level, int alpha, int L, int K, int nd, size_t ext_stride, int B, Ws ws, int *err)
 {
     typedef PassShape<S> P;
-    typedef InnerSmem<S> SM;
+    typedef InnerSmem<S, SUB> SM;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);  // [0], [1]: digit stages; [2]: key stage
     uint64_t *xs = reinterpret_cast<uint64_t *>(smem + SM::X_OFF);
@@ -311,6 +313,7 @@ __global__ void __launch_bounds__(InnerSmem<S>::THREADS, 2)
         }
         __syncthreads();  // digit stage j & 1 and the key stage are free again
         if (threadIdx.x == 0) {
+            fence_proxy_async_smem();  // the CTA's reads of those stages before the copies that refill them
             if (j + 2 < nd) load_digit(j + 2);
             if (j + 1 < nd) load_keys(j + 1);
         }
@@ -671,17 +674,25 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
     // batch (its items run back to back on the same key tile); per item and
     // target limb: one digit word per digit read, two accumulators written
     ProfScope _ps(c, "inner_chunks", (uint64_t)E_ext * 2 * nd + (uint64_t)B * E_ext * (nd + 2));
-    dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
-        constexpr int S = decltype(sv)::value;
-        const dim3 grid(B * ((c.N >> S) / InnerSmem<S>::SUB), E_ext);
-        const size_t smem = InnerSmem<S>::BYTES;
+    auto launch = [&](auto sv, auto subv) {
+        constexpr int S = decltype(sv)::value, SUB = decltype(subv)::value;
+        typedef InnerSmem<S, SUB> SM;
+        const dim3 grid(B * ((c.N >> S) / SUB), E_ext);
         static std::atomic<bool> attr_set{false};
         if (!attr_set.load()) {
-            PPST_CUDA(cudaFuncSetAttribute(k_inner_chunks<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            PPST_CUDA(cudaFuncSetAttribute(k_inner_chunks<S, SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)SM::BYTES));
             attr_set = true;
         }
-        launch_on(c, k_inner_chunks<S>, grid, InnerSmem<S>::THREADS, smem, c.ws_ext, c.ws_d2n, key.d, c.ws_acc,
+        launch_on(c, k_inner_chunks<S, SUB>, grid, SM::THREADS, SM::BYTES, c.ws_ext, c.ws_d2n, key.d, c.ws_acc,
             c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, B, ws, c.d_err);
+    };
+    dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
+        switch (c.inner_sub) {
+        case 4: launch(sv, std::integral_constant<int, 4>{}); break;
+        case 16: launch(sv, std::integral_constant<int, 16>{}); break;
+        default: launch(sv, std::integral_constant<int, 8>{}); break;
+        }
     });
     check_launch("k_inner_chunks");
 }

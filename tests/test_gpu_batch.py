@@ -67,6 +67,7 @@ def test_autotune_picks_a_measured_dnum(tmp_path):
     assert best in (2, 3, 6) and [r["dnum"] for r in table] == [2, 3, 6]
     for r in table:
         assert r["hmult_us"] > 0 and r["rotate_us"] > 0 and r["query_us"] > 0
+        assert r["tile"] in (4, 8, 16) and r["hmult_us"] == min(r["tile_us"].values())
     fastest = min(table, key=lambda r: r["query_us"])["dnum"]
     assert best == fastest
     with open(cache) as f:
@@ -74,6 +75,8 @@ def test_autotune_picks_a_measured_dnum(tmp_path):
     again, _ = autotune.tune(base, cache=cache, candidates=(2, 3, 6), reps=3, query=q)  # from the cache
     assert again == best
     assert autotune.tuned_params(base, cache=cache)["n_p"] == 12 // best
+    prm, tile = autotune.tuned_setup(base, cache=cache)
+    assert prm["dnum"] == best and tile == next(r["tile"] for r in table if r["dnum"] == best)
 
 
 def test_many_queries_deterministic_full_size():

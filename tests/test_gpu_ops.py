@@ -239,3 +239,21 @@ def test_bounded_wait_timeout_is_reported(env):
     with pytest.raises(pp.PpstError) as e:
         ctx.selftest_wait(0)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("tile", [4, 8, 16])
+def test_inner_product_tiles_agree(env, tile):
+    """The inner product's tile (chunks per block) changes speed only: HMult and a
+    rotation bit-exact against the oracle for every tile."""
+    import paper_2508_12093_gb300 as pp
+    ctx, sk, evk, oc, ok = env
+    _, oa, ga = fresh(env, 23)
+    ctx.set_tile(tile)
+    try:
+        same(ctx, ctx.hmult(evk, ga, ga), oc.hmult(oa, oa, ok))
+        same(ctx, ctx.rotate(evk, ga, 4), oc.rotate(oa, 4, ok))
+    finally:
+        ctx.set_tile(8)
+    with pytest.raises(pp.PpstError) as e:
+        ctx.set_tile(5)
+    assert e.value.code == -1
