@@ -280,6 +280,7 @@ __global__ void __launch_bounds__(InnerSmem<S, SUB>::THREADS, InnerSmem<S, SUB>:
         mbar_init(&bar[1], 1);
         mbar_init(&bar[2], 1);
         mbar_fence_init();
+        fence_proxy_async_smem();
         load_digit(0);
         if (nd > 1) load_digit(1);
         load_keys(0);
@@ -452,6 +453,7 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_fence_init();
+        fence_proxy_async_smem();
         mbar_arrive_expect_tx(&bar[0], ad ? 2 * TB : TB);
         bulk_g2s(smem + SM::A_OFF, acc + it * ws.acc + (size_t)k * ext_stride + t0, TB, &bar[0]);
         if (ad) bulk_g2s(smem + SM::D_OFF, ad + t0, TB, &bar[0]);
@@ -561,6 +563,7 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_fence_init();
+        fence_proxy_async_smem();
         mbar_arrive_expect_tx(&bar[0], SM::TILE * 8);
         bulk_g2s(smem + SM::A_OFF, a + (size_t)k * pstride + t0, SM::TILE * 8, &bar[0]);
     }
