@@ -42,10 +42,10 @@ WORKLOAD = ("N=2^16 (32768 slots), 24 Q primes (60+23x50 bit) + 4 special 60-bit
 HMULT_BYTES = (2 * 2 * 24 + 6 * 2 * 28 + 2 * 24) * 65536 * 8
 # DRAM bytes per algorithmic byte of a kernel, from ncu captures: k_inner_chunks
 # in a single-item top-level HMult (python -m paper_2508_12093_gb300.profcase hmult)
-# read 294.1 MB and wrote 20.8 MB against 293.6 MB algorithmic (1.073); with three
-# items (profcase batch3) 541.2 MB against 528.5 MB (1.024). The single-item
+# read 294.1 MB and wrote 20.6 MB against 293.6 MB algorithmic (1.072); with three
+# items (profcase batch3) 540.9 MB against 528.5 MB (1.023). The single-item
 # ratio is used: the larger of the two
-DRAM_PER_ALG = {"inner_chunks": (294.1 + 20.8) / 293.6}
+DRAM_PER_ALG = {"inner_chunks": (294.05 + 20.55) / 293.6}
 
 
 def peaks():
@@ -472,7 +472,7 @@ def main():
                          "frac": achieved / peak if achieved else None,
                          "traffic": (DRAM_PER_ALG[dom] * alg_bytes / max(1, n_dom)) if dom in DRAM_PER_ALG else None,
                          "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per algorithmic byte of "
-                                            "a single-item top-level launch (1.073; 1.024 with three items), times "
+                                            "a single-item top-level launch (1.072; 1.023 with three items), times "
                                             "the algorithmic bytes per launch"
                                             if dom in DRAM_PER_ALG else None),
                          "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
