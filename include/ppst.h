@@ -291,7 +291,7 @@ int ppst_ticket_latency(ppst_server *srv, uint64_t ticket, double *seconds);
  * ntt_cols_fwd, ntt_chunks_fwd, ntt_chunks_inv, ntt_cols_inv (transform
  * passes), modup_cols, inner_chunks, moddown_top, moddown_cols, moddown_chunks
  * (fused key switching), modup, inner_product, moddown_conv, moddown_final
- * (unfused key switching), rescale_bcast, rescale_final, tensor, automorph,
+ * (unfused key switching), rescale_cols, rescale_chunks, tensor, automorph,
  * lincomb, elementwise, copy. ppst_prof_read synchronises, returns the launch
  * count, summed device time and summed algorithmic traffic of one class, and
  * forgets them; the traffic is counted in limbs of N words (8N bytes each), as
