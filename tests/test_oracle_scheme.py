@@ -322,3 +322,22 @@ def test_constant_column_is_outside_the_domain():
     reference flags it; on encrypted data it cannot be detected)."""
     with pytest.raises(ZeroDivisionError), np.errstate(divide="ignore", invalid="ignore"):
         stats.plain_stats(np.full(100, 3.0))
+
+
+def test_sec72_grid_simulated():
+    """The inverse-square-root sweep of Sec. 7.2 (16,384 points in [0.001, 1] and
+    16,384 in [1, 100], pre-normalised by B = 100) through the noise-free
+    simulator: the approximation error alone, against 1/sqrt(x). With the
+    statistics' settings (degree 127, 3 Newton steps) the mean relative error is
+    of the paper's order (5.08e-5 with bootstrapping); with the paper's own
+    settings (degree 511, 6 steps) Newton converges to FP64 precision."""
+    x = workloads.inv_sqrt_grid()
+    assert len(x) == 32768 and x.min() == 0.001 and x.max() == 100.0
+    ev = sim_for(S=32768, levels=24)
+    ref = 1.0 / np.sqrt(x)
+    mre = {}
+    for k, t in ((7, 3), (9, 6)):
+        y = stats.crypto_inv_sqrt(ev, ev.encrypt(x / 100.0), 100.0, k, t)
+        mre[(k, t)] = float(np.mean(np.abs(y.v - ref) / ref))
+    assert 1e-5 < mre[(7, 3)] < 5e-5
+    assert mre[(9, 6)] < 1e-12
