@@ -239,6 +239,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--served", type=int, default=48, help="queries per arrival rate in the served sample (0: skip)")
+    ap.add_argument("--served-cols", type=int, default=SERVED_COLS,
+                    help="lognormal columns in the served pool (the full served workload: 125 + 3 pairs, 10000 "
+                         "queries)")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 64-column batched workload and the dnum autotuner")
     args = ap.parse_args()
@@ -369,7 +372,7 @@ def main():
     distinct_value = len(STATS) * max(3, args.steps // 2) / (s0.elapsed_time(s1) / 1000.0)
     del copies
 
-    srv = served_stream(pp, ctx, sk, evk, ost, args.served) if args.served > 0 else None
+    srv = served_stream(pp, ctx, sk, evk, ost, args.served, args.served_cols) if args.served > 0 else None
     sweep72 = inv_sqrt_sweep(ctx, sk, evk)
     toy = toy_zscore(pp, ost)
     peak, peak_kind = peaks()
@@ -575,7 +578,7 @@ SERVED_PAIRS = 3          # Bernoulli / lognormal column pairs for Pearson corre
 SERVED_BUDGET = 48 << 30  # HBM admission budget of the request loop (bytes)
 
 
-def served_stream(pp, ctx, sk, evk, ost, count):
+def served_stream(pp, ctx, sk, evk, ost, count, ncols=SERVED_COLS):
     """Served form: a seeded Poisson stream of mixed queries over resident
     columns of 1k-1M rows (multi-ciphertext), admitted by HBM budget into the
     continuous-batching request loop at 0.5x, 1x and 2x the one-at-a-time
@@ -585,15 +588,15 @@ def served_stream(pp, ctx, sk, evk, ost, count):
     import numpy as np
     import torch
     rng = np.random.default_rng(workloads.SEEDS["arrival"] + 1)
-    lens = workloads.log_uniform_lengths(SERVED_COLS + SERVED_PAIRS, 1000, 1_000_000)
+    lens = workloads.log_uniform_lengths(ncols + SERVED_PAIRS, 1000, 1_000_000)
     cols, data = [], []
-    for i in range(SERVED_COLS):
+    for i in range(ncols):
         x = workloads.lognormal_column(int(lens[i]), seed=100 + i)
         cols.append(ctx.encrypt_column(evk, x, 200 + i))
         data.append(x)
     pairs = []
     for j in range(SERVED_PAIRS):
-        x, y = workloads.pcc_pair(int(lens[SERVED_COLS + j]), seed=300 + j)
+        x, y = workloads.pcc_pair(int(lens[ncols + j]), seed=300 + j)
         pairs.append((ctx.encrypt_column(evk, x, 400 + j), ctx.encrypt_column(evk, y, 500 + j), x, y))
     kinds = ["zscore", "cv", "skew", "kurt", "pcc"]
     qs = []
@@ -603,7 +606,7 @@ def served_stream(pp, ctx, sk, evk, ost, count):
             j = int(rng.integers(SERVED_PAIRS))
             qs.append((k, pairs[j][0], pairs[j][1], dict(B_x=1.0, B_y=20.0, cheb_log2deg=7, newton_steps=3), ("p", j)))
         else:
-            i = int(rng.integers(SERVED_COLS))
+            i = int(rng.integers(ncols))
             qs.append((k, cols[i], None, dict(OPTS), ("c", i)))
 
     # plain form: one query at a time
@@ -656,7 +659,7 @@ def served_stream(pp, ctx, sk, evk, ost, count):
             "sweep": sweep, "queries": count,
             "max_rel_err_vs_fp64": worst, "hbm_budget_bytes": SERVED_BUDGET, "max_batch": 16,
             "sample": (f"the first {count} queries of a seeded Poisson stream mixing Z-score/CV/skewness/kurtosis/"
-                       f"Pearson uniformly over {SERVED_COLS} lognormal columns and {SERVED_PAIRS} Bernoulli/"
+                       f"Pearson uniformly over {ncols} lognormal columns and {SERVED_PAIRS} Bernoulli/"
                        f"lognormal pairs of log-uniform 1k-1M rows (N=2^16, multi-ciphertext), keys and "
                        f"columns resident; arrivals at 0.5x, 1x and 2x the one-at-a-time capacity (value: 2x, "
                        f"latency: 1x)")}
