@@ -68,3 +68,23 @@ def test_autotune_family_and_bytes(dnum, mb):
     assert abs(autotune.ks_bytes(p) / 1e6 - mb) < 0.01
     with pytest.raises(ValueError):
         autotune.with_dnum(workloads.PARAMS["n16_d6"], 5)
+
+
+def test_batched_workload_shape():
+    """The 64-column batched workload: five statistics per column pair (Z-score,
+    CV, skewness and kurtosis of each column, Pearson of the pair), B = 20 for the
+    lognormal-shaped columns and 1 for the Bernoulli ones."""
+    import bench
+    cols = [object() for _ in range(bench.BATCH_COLS)]
+    qs = bench.batched_queries(cols)
+    assert len(qs) == 4 * 64 + 32
+    by = {}
+    for q in qs:
+        by.setdefault(q[0], []).append(q)
+    assert {k: len(v) for k, v in by.items()} == {"zscore": 64, "cv": 64, "skew": 64, "kurt": 64, "pcc": 32}
+    for q in qs:
+        if q[0] == "pcc":
+            i, j = q[4]
+            assert j == i + 1 and i % 2 == 0 and q[3]["B_x"] == 20.0 and q[3]["B_y"] == 1.0
+        else:
+            assert q[3]["B_x"] == (20.0 if q[4][0] % 2 == 0 else 1.0)
