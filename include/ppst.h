@@ -120,8 +120,6 @@ typedef struct {
 int ppst_ctx_create(const ppst_params *params, const ppst_allocator *alloc, void *stream,
                     ppst_ctx **out);
 const char *ppst_last_error(const ppst_ctx *ctx);
-/* primes_out[0 .. n_q + n_p) = q_0 .. q_L, p_0 .. p_{K-1}; *n_primes = n_q + n_p.
- * Writes at most `cap` primes. */
 /* Tile of the key-switching inner product (no counterpart in the paper): the
  * transform chunks each block owns, 4, 8 (default) or 16 (PPST_E_ARG
  * otherwise). Changes speed only, never results; the autotuner measures it. */
@@ -133,6 +131,10 @@ int ppst_ctx_set_tile(ppst_ctx *ctx, uint32_t inner_sub);
  * next synchronising call (ppst_sync, a decryption, an export) returns
  * PPST_E_CUDA and clears the word; the context stays usable. */
 int ppst_selftest_wait(ppst_ctx *ctx, uint32_t timeout_us);
+/* The prime chain of the context (Sec. 7.1 fixes only its total size; the
+ * rule that picks the primes is the library's): primes_out[0 .. n_q + n_p) =
+ * q_0 .. q_L, p_0 .. p_{K-1}; *n_primes = n_q + n_p. Writes at most `cap`
+ * primes (primes_out may be NULL to query the count). */
 int ppst_ctx_primes(const ppst_ctx *ctx, uint64_t *primes_out, size_t cap, uint32_t *n_primes);
 /* Block until all GPU work issued on the context's stream has finished. */
 int ppst_sync(ppst_ctx *ctx);
@@ -217,15 +219,30 @@ int ppst_hmult(ppst_ctx *ctx, const ppst_evk *evk, const ppst_ct *a, const ppst_
  * level; its contents, level and scale are replaced; it must not be a or b).
  * Every temporary lives in one static 32 MiB device array that each GPU
  * loading the library holds until exit; parameter sets needing more return
- * PPST_E_ARG (N = 2^12 with 20 primes fits; N = 2^16 does not). The first
- * call on a device looks up the array's address there (call it once before
- * any stream capture). Calls share the array: calls whose GPU work overlaps
+ * PPST_E_ARG (N = 2^12 with 20 primes fits; N = 2^16 does not). Creating a
+ * context looks up the array's address on its device, which is when the
+ * driver commits the array's memory there; the kernels a call launches load
+ * on their first launch, so make one call before the free memory is handed to
+ * another allocator. Calls share the array: calls whose GPU work overlaps
  * race. It calls no device allocator: not cudaMalloc/cudaFree, not the
- * context's pool, not the ppst_allocator. */
+ * context's pool, not the ppst_allocator. On an error `out` is unchanged. */
 int ppst_hmult_noalloc(ppst_ctx *ctx, const ppst_evk *evk, const ppst_ct *a, const ppst_ct *b,
                        ppst_ct *out);
 /* Rot: slot j of the result = slot j + r of the input (Galois key needed). */
 int ppst_rotate(ppst_ctx *ctx, const ppst_evk *evk, const ppst_ct *a, int32_t r, ppst_ct **out);
+/* Batched Mul(C) and Rot (Sec. 3.1; batching has no counterpart in the paper):
+ * n = 1 .. 16 independent operations whose key switches share one launch
+ * sequence, so each switching-key tile is read from HBM once for the batch.
+ * hmult_batch: out[i] = a[i] * b[i]; every pair must have the same level
+ * min(level(a[i]), level(b[i])). rotate_batch: out[i] = Rot(a[i], r); every
+ * a[i] at one level. `out` has room for n handles; on error every out[i] is
+ * NULL. Results are bit-identical to n single calls. Errors: PPST_E_ARG
+ * (n out of range, levels differ, bad handle), PPST_E_DEPTH, PPST_E_STATE
+ * (missing key), PPST_E_OOM, PPST_E_CUDA. */
+int ppst_hmult_batch(ppst_ctx *ctx, const ppst_evk *evk, size_t n, const ppst_ct *const *a,
+                     const ppst_ct *const *b, ppst_ct **out);
+int ppst_rotate_batch(ppst_ctx *ctx, const ppst_evk *evk, size_t n, const ppst_ct *const *a, int32_t r,
+                      ppst_ct **out);
 /* Rotate-and-sum over all N/2 slots (every slot = the total). */
 int ppst_rotsum(ppst_ctx *ctx, const ppst_evk *evk, const ppst_ct *a, ppst_ct **out);
 int ppst_rescale(ppst_ctx *ctx, const ppst_ct *a, ppst_ct **out);

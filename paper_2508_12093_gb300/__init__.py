@@ -388,6 +388,23 @@ class Context:
     def rotate(self, evk, a, r):
         return self._new(lib.ppst_rotate, evk.ptr, a.ptr, r)
 
+    def hmult_batch(self, evk, a_list, b_list):
+        """ppst_hmult_batch: a_i * b_i for up to 16 pairs in one key-switch launch sequence."""
+        n = len(a_list)
+        pa = (ctypes.c_void_p * n)(*[x.ptr for x in a_list])
+        pb = (ctypes.c_void_p * n)(*[x.ptr for x in b_list])
+        out = (ctypes.c_void_p * n)()
+        self._check(lib.ppst_hmult_batch(self.ptr, evk.ptr, n, pa, pb, out))
+        return [Ciphertext(self, out[i]) for i in range(n)]
+
+    def rotate_batch(self, evk, a_list, r):
+        """ppst_rotate_batch: Rot(a_i, r) for up to 16 ciphertexts in one launch sequence."""
+        n = len(a_list)
+        pa = (ctypes.c_void_p * n)(*[x.ptr for x in a_list])
+        out = (ctypes.c_void_p * n)()
+        self._check(lib.ppst_rotate_batch(self.ptr, evk.ptr, n, pa, int(r), out))
+        return [Ciphertext(self, out[i]) for i in range(n)]
+
     def rotsum(self, evk, a):
         return self._new(lib.ppst_rotsum, evk.ptr, a.ptr)
 

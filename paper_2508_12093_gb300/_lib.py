@@ -73,6 +73,8 @@ SIGNATURES = {
     "ppst_hmult": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, PP]),
     "ppst_hmult_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ppst_rotate": (c_int, [c_void_p, c_void_p, c_void_p, c_i32, PP]),
+    "ppst_hmult_batch": (c_int, [c_void_p, c_void_p, c_size_t, PP, PP, PP]),
+    "ppst_rotate_batch": (c_int, [c_void_p, c_void_p, c_size_t, PP, c_i32, PP]),
     "ppst_rotsum": (c_int, [c_void_p, c_void_p, c_void_p, PP]),
     "ppst_selftest_wait": (c_int, [c_void_p, c_u32]),
     "ppst_ctx_set_tile": (c_int, [c_void_p, c_u32]),

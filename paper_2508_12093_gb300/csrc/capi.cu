@@ -459,6 +459,49 @@ int ppst_rotate(ppst_ctx *ctx, const ppst_evk *evk, const ppst_ct *a, int32_t r,
     })
 }
 
+int ppst_hmult_batch(ppst_ctx *ctx, const ppst_evk *evk, size_t n, const ppst_ct *const *a,
+                     const ppst_ct *const *b, ppst_ct **out)
+{
+    Ctx *c = (Ctx *)ctx;
+    if (!ok(c, TAG_CTX)) return PPST_E_ARG;
+    if (!out || !a || !b) return c->fail(PPST_E_ARG, "null argument");
+    for (size_t i = 0; i < n; i++) out[i] = nullptr;
+    return guard(c, [&] {
+        const EvkObj *k = (const EvkObj *)evk;
+        REQ(ok(k, TAG_EVK), "bad key");
+        REQ(n >= 1 && n <= 16, "hmult batch: 1 to 16 pairs");
+        std::vector<const CtObj *> as(n), bs(n);
+        for (size_t i = 0; i < n; i++) {
+            as[i] = (const CtObj *)a[i];
+            bs[i] = (const CtObj *)b[i];
+            REQ(ok(as[i], TAG_CT) && as[i]->ctx == c && ok(bs[i], TAG_CT) && bs[i]->ctx == c, "bad ciphertext");
+        }
+        std::vector<CtObj *> r = ev_hmult_batch(*c, *k, as, bs);
+        for (size_t i = 0; i < n; i++) out[i] = (ppst_ct *)r[i];
+    });
+}
+
+int ppst_rotate_batch(ppst_ctx *ctx, const ppst_evk *evk, size_t n, const ppst_ct *const *a, int32_t r,
+                      ppst_ct **out)
+{
+    Ctx *c = (Ctx *)ctx;
+    if (!ok(c, TAG_CTX)) return PPST_E_ARG;
+    if (!out || !a) return c->fail(PPST_E_ARG, "null argument");
+    for (size_t i = 0; i < n; i++) out[i] = nullptr;
+    return guard(c, [&] {
+        const EvkObj *k = (const EvkObj *)evk;
+        REQ(ok(k, TAG_EVK), "bad key");
+        REQ(n >= 1 && n <= 16, "rotate batch: 1 to 16 ciphertexts");
+        std::vector<const CtObj *> as(n);
+        for (size_t i = 0; i < n; i++) {
+            as[i] = (const CtObj *)a[i];
+            REQ(ok(as[i], TAG_CT) && as[i]->ctx == c, "bad ciphertext");
+        }
+        std::vector<CtObj *> o = ev_rotate_batch(*c, *k, as, r);
+        for (size_t i = 0; i < n; i++) out[i] = (ppst_ct *)o[i];
+    });
+}
+
 int ppst_rotsum(ppst_ctx *ctx, const ppst_evk *evk, const ppst_ct *a, ppst_ct **out)
 {
     CT_OP(rotsum, {

@@ -601,6 +601,9 @@ Ctx *ctx_create(const ppst_params &pin, const ppst_allocator *alloc, cudaStream_
             }
             c->d_md_const = upload(*c, c->md_const);
         }
+        // commit the allocation-free HMult's static scratch on this device now,
+        // while allocating is still possible (see noalloc.cu)
+        noalloc_scratch_on_current_device();
         PPST_CUDA(cudaStreamSynchronize(stream));
     } catch (...) {
         ctx_destroy(c);

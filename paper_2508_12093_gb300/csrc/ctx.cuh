@@ -300,6 +300,9 @@ CtObj *ev_lin_comb(Ctx &c, const std::vector<const CtObj *> &cts, const std::vec
 CtObj *ev_hmult(Ctx &c, const EvkObj &k, const CtObj &a, const CtObj &b);
 CtObj *ev_rotate(Ctx &c, const EvkObj &k, const CtObj &a, int r);
 // up to 16 independent HMults / rotations in one pass of launches (pairs at one level)
+// device address of the allocation-free HMult's static scratch array on the
+// current device (looked up once per device; noalloc.cu)
+uint64_t *noalloc_scratch_on_current_device();
 std::vector<CtObj *> ev_hmult_batch(Ctx &c, const EvkObj &k, const std::vector<const CtObj *> &as,
                                     const std::vector<const CtObj *> &bs);
 std::vector<CtObj *> ev_rotate_batch(Ctx &c, const EvkObj &k, const std::vector<const CtObj *> &as, int r);

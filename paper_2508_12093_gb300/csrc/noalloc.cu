@@ -9,13 +9,18 @@
 // buffers) carved from one static device array of NOALLOC_BYTES, which every
 // GPU that loads this library holds until the process exits.
 //
-// Set-up: the first call on each device looks up that device's address of the
-// array (cudaGetSymbolAddress) with the device current, and caches it; that
-// first call should therefore come before any stream capture. All calls share
-// the array and it keeps the last call's contents; no word of it is read
-// before the same call writes it, so nothing needs clearing. Calls whose GPU
-// work overlaps (other threads, other streams, other contexts on the same
-// device) race on the array.
+// Set-up: creating a context looks up its device's address of the array
+// (cudaGetSymbolAddress, with the device current) and caches it. That lookup
+// loads this file's module, which is when the driver commits the array's
+// memory on the device, so the 32 MiB are taken while the caller can still
+// allocate. The kernels a call launches are loaded on their first launch
+// (CUDA's lazy loading), so a caller about to give the free memory away makes
+// one call first. All calls share the array and it keeps the last call's
+// contents; no word of it is read before the same call writes it, so nothing
+// needs clearing. Calls whose GPU work overlaps (other threads, other
+// streams, other contexts on the same device) race on the array. On an
+// error the output ciphertext is left as it was: the result is built in the
+// array and copied into the output only once every kernel has been issued.
 #include <mutex>
 
 #include "ctx.cuh"
@@ -30,7 +35,7 @@ static __device__ __align__(256) uint64_t g_noalloc_scratch[NOALLOC_WORDS];
 static std::mutex g_noalloc_mu;
 static std::map<int, uint64_t *> g_noalloc_addr;  // device -> address of the array there
 
-static uint64_t *noalloc_scratch_on_current_device()
+uint64_t *noalloc_scratch_on_current_device()
 {
     int dev = 0;
     PPST_CUDA(cudaGetDevice(&dev));
@@ -44,11 +49,12 @@ static uint64_t *noalloc_scratch_on_current_device()
 }
 
 // words of scratch: pre-rescale product [2][L+1][N], d2 [L+1][N],
-// digits [dnum][L+1+K][N], accumulators [2][L+1+K][N], conversion [2][L+1][N]
+// digits [dnum][L+1+K][N], accumulators [2][L+1+K][N], conversion [2][L+1][N],
+// rescaled result [2][L+1][N]
 static size_t noalloc_words(const Ctx &c)
 {
     const size_t N = c.N, q = c.L + 1, e = c.ext_rows();
-    return (2 * q + q + (size_t)c.dnum * e + 2 * e + 2 * q) * N;
+    return (2 * q + q + (size_t)c.dnum * e + 2 * e + 2 * q + 2 * q) * N;
 }
 
 void hmult_noalloc(Ctx &c, const EvkObj &k, const CtObj &a, const CtObj &b, CtObj &out)
@@ -84,9 +90,15 @@ void hmult_noalloc(Ctx &c, const EvkObj &k, const CtObj &a, const CtObj &b, CtOb
         ntt_fwd(c, me);
         k_inner_product(c, ext, k.relin, lv, acc);
         k_moddown(c, acc, lv, tmp.c0(), tmp.c1(), tmp.c0(), tmp.c1());
+        CtObj res;  // the rescaled product, also inside the static array
+        res.ctx = &c;
+        res.d = conv + 2 * q * N;
+        res.level = lv - 1;
+        k_rescale(c, tmp, res);
+        // only now does the caller's ciphertext change (a device-to-device copy, no allocation)
+        PPST_CUDA(cudaMemcpyAsync(out.d, res.d, 2 * q * N * sizeof(uint64_t), cudaMemcpyDeviceToDevice, c.stream));
         out.level = lv - 1;
         out.scale = (a.scale * b.scale) / (double)c.primes[lv];
-        k_rescale(c, tmp, out);
     } catch (...) {
         c.ws_d2 = sv[0];
         c.ws_ext = sv[1];

@@ -6,6 +6,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+TESTS = os.path.join(ROOT, "tests")
+if TESTS not in sys.path:
+    sys.path.insert(0, TESTS)
 
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 
@@ -13,6 +16,7 @@ GOLDEN = os.path.join(ROOT, "tests", "golden")
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+    config.addinivalue_line("markers", "oracle16(*jobs): needs these N = 2^16 oracle jobs (tests/oracle_jobs.py)")
 
 
 def read_golden(name):
@@ -27,3 +31,22 @@ def read_golden(name):
             parts = ln.split()
             rows[parts[0]] = parts[1:]
     return rows, lines
+
+
+def pytest_collection_finish(session):
+    """Start the N = 2^16 oracle jobs in spawned processes as soon as a test
+    that needs them is selected, so they run while the other tests do."""
+    names = set()
+    for item in session.items:
+        m = item.get_closest_marker("oracle16")
+        if m is not None:
+            names.update(m.args)
+    if names:
+        import oracle_jobs
+        oracle_jobs.start(sorted(names))
+
+
+def pytest_sessionfinish(session, exitstatus):
+    mod = sys.modules.get("oracle_jobs")
+    if mod is not None:
+        mod.shutdown()

@@ -72,6 +72,47 @@ def test_schedule_parity_small(deep, stat, n):
     assert rep["depth_used"] == DEEP12["n_q"] - 1 - rep["level_out"]
 
 
+# the benchmark's approximation settings (degree 127, 3 Newton steps): depth 19 for
+# skewness and kurtosis, the whole 20-prime chain
+OPTS12_BENCH = dict(B_x=20.0, B_y=20.0, cheb_log2deg=7, newton_steps=3)
+
+
+@pytest.mark.parametrize("stat", ["skew", "kurt", "cv", "zscore", "pcc"])
+def test_schedule_parity_benchmark_settings(deep, stat):
+    """Every statistic at degree 127 + 3 Newton steps (one Chebyshev split
+    recursion deeper than degree 31) on a ragged two-ciphertext column: result
+    limbs bit-exact against the oracle."""
+    from oracle import stats as ost
+    ctx, sk, evk, oc, ok = deep
+    n = 2048 + 301
+    o = OPTS12_BENCH
+    if stat == "pcc":
+        x, y = workloads.pcc_pair(n, seed=16)
+        ox, cx = shared_column(deep, x, 61)
+        oy, cy = shared_column(deep, y, 62)
+        res = ctx.query(evk, "pcc", cx, cy, opts=dict(o, B_x=1.0))
+        want = [ost.pcc(ost.CkksEv(oc, ok), ox, oy, n, 1.0, 20.0, o["cheb_log2deg"], o["newton_steps"])]
+        ref = ost.plain_stats(x, y)["pcc"]
+    else:
+        x = workloads.lognormal_column(n, seed=15)
+        ox, cx = shared_column(deep, x, 63)
+        res = ctx.query(evk, stat, cx, opts=o)
+        f = {"skew": ost.skew, "kurt": ost.kurt, "cv": ost.cv, "zscore": ost.znorm}[stat]
+        want = f(ost.CkksEv(oc, ok), ox, n, 20.0, o["cheb_log2deg"], o["newton_steps"])
+        want = want if isinstance(want, list) else [want]
+        ref = ost.plain_stats(x)[stat]
+    got = res.cts()
+    assert len(got) == len(want)
+    for g, w in zip(got, want):
+        check_same(ctx, g, w)
+    vals, rep = ctx.decrypt(sk, res)
+    if stat == "zscore":
+        assert np.abs(vals - ref).max() / np.abs(ref).max() < TOL
+    else:
+        assert abs(vals[0] / ref - 1) < TOL
+    assert rep["depth_used"] == {"skew": 19, "kurt": 19, "cv": 17, "zscore": 17, "pcc": 18}[stat]
+
+
 @pytest.mark.parametrize("n", [2048, 3000])
 def test_pcc_parity_small(deep, n):
     from oracle import stats as ost

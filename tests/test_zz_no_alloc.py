@@ -11,6 +11,7 @@ import ctypes
 
 import numpy as np
 import pytest
+import torch
 
 import workloads
 
@@ -36,12 +37,17 @@ def test_noalloc_hmult_equals_hmult_twice():
     # a ciphertext the caller already owns; its contents get replaced
     out = ctx.encrypt_ints(evk, np.zeros(ctx.N, dtype=np.int64), 13, 0, 2.0 ** 40)
     cases = [(a, b), (ctx.drop(b, 7), ctx.drop(a, 9))]
+    # a first call loads the kernels it launches (CUDA loads kernels lazily)
+    assert lib.ppst_hmult_noalloc(ctx.ptr, evk.ptr, a.ptr, b.ptr, out.ptr) == 0
+    ctx.sync()
     for ca, cb in cases:
         in_use0, cached0 = ctx.mem_info()
+        free0 = torch.cuda.mem_get_info()[0]
         rc = lib.ppst_hmult_noalloc(ctx.ptr, evk.ptr, ca.ptr, cb.ptr, out.ptr)
         assert rc == 0, lib.ppst_last_error(ctx.ptr)
         ctx.sync()
         assert ctx.mem_info() == (in_use0, cached0), "the pool was touched"
+        assert torch.cuda.mem_get_info()[0] == free0, "device memory was allocated"
         want = ctx.hmult(evk, ca, cb)
         g0, g1, glv, gsc = export(ctx, out)
         w0, w1, wlv, wsc = export(ctx, want)
@@ -65,3 +71,9 @@ def test_noalloc_rejects_oversized_parameters_and_aliasing():
     c = small.encrypt_column(evk2, workloads.uniform_column(100, seed=4), 1).cts()[0]
     d = small.encrypt_ints(evk2, np.zeros(small.N, dtype=np.int64), 2, 0, 2.0 ** 40)
     assert lib.ppst_hmult_noalloc(small.ptr, evk2.ptr, d.ptr, c.ptr, d.ptr) == -1   # out aliases an input
+    # a call that fails leaves the output as it was
+    before = small.ct_export(d)
+    low = small.drop(c, 0)
+    assert lib.ppst_hmult_noalloc(small.ptr, evk2.ptr, low.ptr, low.ptr, d.ptr) == -2
+    after = small.ct_export(d)
+    assert before[2:] == after[2:] and np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
