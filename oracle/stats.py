@@ -23,6 +23,8 @@ Readings where the paper is silent (the same on the GPU side):
 * Newton's three products are associated as (x' y)(y y): same products as
   Alg. 2, depth 2 per step instead of 3.
 * Columns longer than one ciphertext are summed before one rotate-and-sum;
+  the centred sums of skewness, kurtosis and PCC, consumed only by their final
+  product, are dropped to that product's level before being reduced;
   padding slots are zero and their contribution to the centred moments
   ((-mu)^p per pad) is subtracted with integer multiples of mu^p.
 """
@@ -169,14 +171,24 @@ def variance(ev, cts, n, B, R):
     return ev.sub(a, ev.hmult(m, m))
 
 
-def _centred_power_sum(ev, cts, mu, power):
+def _centred_power_terms(ev, cts, mu, power):
+    """sum over the column's ciphertexts of (x - mu)^power, slot by slot (not
+    yet reduced over the slots)."""
     acc = None
     for ct in cts:
         x1 = ev.sub(ct, mu)
         x2 = ev.hmult(x1, x1)
         xp = ev.hmult(x2, x2) if power == 4 else ev.hmult(x2, x1)
         acc = xp if acc is None else ev.add(acc, xp)
-    return ev.rotsum(acc)
+    return acc
+
+
+def _rotsum_at(ev, a, level):
+    """Rotate-and-sum of `a` after dropping it to `level` (never above its own).
+    Sec. 6.1 leaves open at which level the sums are reduced; a sum whose value
+    is consumed only by a product many levels lower is dropped to that level
+    first, so its rotations switch keys over fewer limbs."""
+    return ev.rotsum(ev.drop(a, min(level, ev.level(a))))
 
 
 def znorm(ev, cts, n, B, k, t):
@@ -193,15 +205,17 @@ def kurt(ev, cts, n, B, k, t):
     not excess, kurtosis)."""
     R = ev.rotsum(col_sum(ev, cts))
     mu = ev.mul_const(R, 1.0 / n)
-    X = _centred_power_sum(ev, cts, mu, 4)
+    S4 = _centred_power_terms(ev, cts, mu, 4)
+    inv = crypto_inv_sqrt(ev, variance(ev, cts, n, B, R), B * B, k, t)
+    inv2 = ev.hmult(inv, inv)
+    inv4 = ev.hmult(inv2, inv2)
+    X = _rotsum_at(ev, S4, ev.level(inv4) + 1)
     pads = len(cts) * ev.slots() - n
     if pads:
         mu2 = ev.hmult(mu, mu)
         X = ev.sub(X, ev.mul_int(ev.hmult(mu2, mu2), pads))
     num = ev.mul_const(X, 1.0 / n)
-    inv = crypto_inv_sqrt(ev, variance(ev, cts, n, B, R), B * B, k, t)
-    inv2 = ev.hmult(inv, inv)
-    return ev.hmult(num, ev.hmult(inv2, inv2))
+    return ev.hmult(num, inv4)
 
 
 def skew(ev, cts, n, B, k, t):
@@ -209,14 +223,15 @@ def skew(ev, cts, n, B, k, t):
     Mean((x - mu)^3) * CryptoInvSqrt(Variance(x, B), B^2)^3."""
     R = ev.rotsum(col_sum(ev, cts))
     mu = ev.mul_const(R, 1.0 / n)
-    X = _centred_power_sum(ev, cts, mu, 3)
+    S3 = _centred_power_terms(ev, cts, mu, 3)
+    inv = crypto_inv_sqrt(ev, variance(ev, cts, n, B, R), B * B, k, t)
+    inv3 = ev.hmult(ev.hmult(inv, inv), inv)
+    X = _rotsum_at(ev, S3, ev.level(inv3) + 1)
     pads = len(cts) * ev.slots() - n
     if pads:
         mu2 = ev.hmult(mu, mu)
         X = ev.add(X, ev.mul_int(ev.hmult(mu2, mu), pads))
     num = ev.mul_const(X, 1.0 / n)
-    inv = crypto_inv_sqrt(ev, variance(ev, cts, n, B, R), B * B, k, t)
-    inv3 = ev.hmult(ev.hmult(inv, inv), inv)
     return ev.hmult(num, inv3)
 
 
@@ -241,13 +256,13 @@ def pcc(ev, xcts, ycts, n, Bx, By, k, t):
     for xc, yc in zip(xcts, ycts):
         p = ev.hmult(ev.sub(xc, mux), ev.sub(yc, muy))
         acc = p if acc is None else ev.add(acc, p)
-    Cs = ev.rotsum(acc)
+    ix = crypto_inv_sqrt(ev, variance(ev, xcts, n, Bx, Rx), Bx * Bx, k, t)
+    iy = crypto_inv_sqrt(ev, variance(ev, ycts, n, By, Ry), By * By, k, t)
+    Cs = _rotsum_at(ev, acc, min(ev.level(ix), ev.level(iy)) + 1)
     pads = len(xcts) * ev.slots() - n
     if pads:
         Cs = ev.sub(Cs, ev.mul_int(ev.hmult(mux, muy), pads))
     cov = ev.mul_const(Cs, 1.0 / n)
-    ix = crypto_inv_sqrt(ev, variance(ev, xcts, n, Bx, Rx), Bx * Bx, k, t)
-    iy = crypto_inv_sqrt(ev, variance(ev, ycts, n, By, Ry), By * By, k, t)
     return ev.hmult(ev.hmult(cov, ix), iy)
 
 

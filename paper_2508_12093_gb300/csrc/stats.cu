@@ -689,12 +689,18 @@ H col_inv_sd(Ev &ev, const Col &x, size_t n, double B, const H &R, const void *k
                            [&] { return crypto_inv_sqrt(ev, col_var(ev, x, n, B, R, kx), B * B, k, t); });
 }
 
-H centred_power_sum(Ev &ev, const Col &x, const H &mu, int power)
+// sum over the column's ciphertexts of (x - mu)^power, slot by slot (not yet reduced)
+H centred_power_terms(Ev &ev, const Col &x, const H &mu, int power)
 {
     const Col x1 = ev.sub_v(x, mu);
     const Col x2 = ev.hmult_v(x1, x1);
-    return ev.rotsum(ev.sum(ev.hmult_v(x2, power == 4 ? x2 : x1)));
+    return ev.sum(ev.hmult_v(x2, power == 4 ? x2 : x1));
 }
+
+// rotate-and-sum of a after dropping it to `level` (never above its own): a sum
+// consumed only by a product many levels lower is reduced at that level, so its
+// rotations switch keys over fewer limbs (Sec. 6.1 leaves the level open)
+H rotsum_at(Ev &ev, const H &a, int level) { return ev.rotsum(ev.drop(a, std::min(level, ev.level(a)))); }
 
 Col znorm(Ev &ev, const Col &x, size_t n, double B, int k, int t, const void *kx)
 {
@@ -708,31 +714,34 @@ H kurt(Ev &ev, const Col &x, size_t n, double B, int k, int t, const void *kx)
 {
     H R = col_rsum(ev, x, kx);
     H mu = ev.mul_const(R, 1.0 / (double)n);
-    H X = centred_power_sum(ev, x, mu, 4);
+    H S4 = centred_power_terms(ev, x, mu, 4);
+    H inv = col_inv_sd(ev, x, n, B, R, kx, k, t);
+    H inv2 = ev.hmult(inv, inv);
+    H inv4 = ev.hmult(inv2, inv2);
+    H X = rotsum_at(ev, S4, ev.level(inv4) + 1);
     const int64_t pads = (int64_t)(x.size() * (size_t)ev.c.S) - (int64_t)n;
     if (pads) {
         H mu2 = ev.hmult(mu, mu);
         X = ev.sub(X, ev.mul_int(ev.hmult(mu2, mu2), pads));
     }
     H num = ev.mul_const(X, 1.0 / (double)n);
-    H inv = col_inv_sd(ev, x, n, B, R, kx, k, t);
-    H inv2 = ev.hmult(inv, inv);
-    return ev.hmult(num, ev.hmult(inv2, inv2));
+    return ev.hmult(num, inv4);
 }
 
 H skew(Ev &ev, const Col &x, size_t n, double B, int k, int t, const void *kx)
 {
     H R = col_rsum(ev, x, kx);
     H mu = ev.mul_const(R, 1.0 / (double)n);
-    H X = centred_power_sum(ev, x, mu, 3);
+    H S3 = centred_power_terms(ev, x, mu, 3);
+    H inv = col_inv_sd(ev, x, n, B, R, kx, k, t);
+    H inv3 = ev.hmult(ev.hmult(inv, inv), inv);
+    H X = rotsum_at(ev, S3, ev.level(inv3) + 1);
     const int64_t pads = (int64_t)(x.size() * (size_t)ev.c.S) - (int64_t)n;
     if (pads) {
         H mu2 = ev.hmult(mu, mu);
         X = ev.add(X, ev.mul_int(ev.hmult(mu2, mu), pads));
     }
     H num = ev.mul_const(X, 1.0 / (double)n);
-    H inv = col_inv_sd(ev, x, n, B, R, kx, k, t);
-    H inv3 = ev.hmult(ev.hmult(inv, inv), inv);
     return ev.hmult(num, inv3);
 }
 
@@ -753,12 +762,13 @@ H pcc(Ev &ev, const Col &x, const Col &y, size_t n, double Bx, double By, int k,
     H Ry = col_rsum(ev, y, ky);
     H mux = ev.mul_const(Rx, 1.0 / (double)n);
     H muy = ev.mul_const(Ry, 1.0 / (double)n);
-    H Cs = ev.rotsum(ev.sum(ev.hmult_v(ev.sub_v(x, mux), ev.sub_v(y, muy))));
+    H P = ev.sum(ev.hmult_v(ev.sub_v(x, mux), ev.sub_v(y, muy)));
+    H ix = col_inv_sd(ev, x, n, Bx, Rx, kx, k, t);
+    H iy = col_inv_sd(ev, y, n, By, Ry, ky, k, t);
+    H Cs = rotsum_at(ev, P, std::min(ev.level(ix), ev.level(iy)) + 1);
     const int64_t pads = (int64_t)(x.size() * (size_t)ev.c.S) - (int64_t)n;
     if (pads) Cs = ev.sub(Cs, ev.mul_int(ev.hmult(mux, muy), pads));
     H cov = ev.mul_const(Cs, 1.0 / (double)n);
-    H ix = col_inv_sd(ev, x, n, Bx, Rx, kx, k, t);
-    H iy = col_inv_sd(ev, y, n, By, Ry, ky, k, t);
     return ev.hmult(ev.hmult(cov, ix), iy);
 }
 

@@ -292,6 +292,32 @@ def test_znorm_on_ckks_cfg1_shape():
     assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-3
 
 
+@pytest.mark.slow
+def test_kurtosis_on_ckks_reduced_at_consumer_level():
+    """Kurtosis on the exact CKKS oracle (N = 2^12, 20 Q primes, depth 19 at
+    degree 127 + 3 Newton steps) with the centred fourth-power sum reduced at
+    the level of its final product (level 2 here, not 16): the rotations at a
+    low level still give the statistic within 1e-3 of FP64, and the schedule
+    reaches level 0 exactly."""
+    prm = ckks.Params(log_n=12, n_q=20, n_p=2, dnum=10, q0_bits=60, q_bits=40, p_bits=60, log_scale=40)
+    c = ckks.Ckks(prm)
+    keys = c.keygen(2, rotations=[1 << i for i in range(prm.log_n - 1)])
+    n = prm.S + 301
+    x = workloads.lognormal_column(n, seed=15)
+    cts = c.encrypt_column(keys["pk"], x, 63)
+    ev = stats.CkksEv(c, keys)
+    levels = []
+    rotsum = ev.rotsum
+    ev.rotsum = lambda a: (levels.append(a.level), rotsum(a))[1]
+    r = stats.kurt(ev, cts, n, 20.0, 7, 3)
+    assert r.level == 0
+    # Mean's sum at the top, Variance's two levels down, the fourth-power sum at
+    # level 2 (the product with inv^4 at level 1 consumes it)
+    assert sorted(levels) == [2, 17, 19]
+    got = c.decrypt(keys["s"], r)[0]
+    assert abs(got / stats.plain_stats(x)["kurt"] - 1) < 1e-3
+
+
 def test_symmetric_column_has_zero_skew():
     """Data symmetric about its mean: the plain skewness is 0 and the simulated
     schedule's numerator (the centred third-moment sum) vanishes, so the
