@@ -60,10 +60,43 @@ __host__ __device__ __forceinline__ uint64_t mont_redc(uint64_t hi, uint64_t lo,
     return hi < mh ? r + q : r;
 }
 
+// the full 128-bit product a b = hi 2^64 + lo. On the device the four 32 x 32-bit
+// partial products are summed with carry chains once, instead of computing
+// the low and the high 64 bits separately (both need the cross terms).
+__host__ __device__ __forceinline__ void mul128(uint64_t a, uint64_t b, uint64_t &lo, uint64_t &hi)
+{
+#ifdef __CUDA_ARCH__
+    asm("{\n\t"
+        ".reg .u32 a0, a1, b0, b1, w0, w1, w2, w3;\n\t"
+        "mov.b64 {a0, a1}, %2;\n\t"
+        "mov.b64 {b0, b1}, %3;\n\t"
+        "mul.lo.u32 w0, a0, b0;\n\t"
+        "mul.hi.u32 w1, a0, b0;\n\t"
+        "mul.lo.u32 w2, a1, b1;\n\t"
+        "mul.hi.u32 w3, a1, b1;\n\t"
+        "mad.lo.cc.u32 w1, a0, b1, w1;\n\t"
+        "madc.hi.cc.u32 w2, a0, b1, w2;\n\t"
+        "addc.u32 w3, w3, 0;\n\t"
+        "mad.lo.cc.u32 w1, a1, b0, w1;\n\t"
+        "madc.hi.cc.u32 w2, a1, b0, w2;\n\t"
+        "addc.u32 w3, w3, 0;\n\t"
+        "mov.b64 %0, {w0, w1};\n\t"
+        "mov.b64 %1, {w2, w3};\n\t"
+        "}"
+        : "=l"(lo), "=l"(hi)
+        : "l"(a), "l"(b));
+#else
+    lo = a * b;
+    hi = mulhi64(a, b);
+#endif
+}
+
 // a b 2^-64 mod q for a, b < q
 __host__ __device__ __forceinline__ uint64_t mont_mul(uint64_t a, uint64_t b, uint64_t q, uint64_t qinv)
 {
-    return mont_redc(mulhi64(a, b), a * b, q, qinv);
+    uint64_t lo, hi;
+    mul128(a, b, lo, hi);
+    return mont_redc(hi, lo, q, qinv);
 }
 
 // a b mod q for a, b < q (two Montgomery reductions)
@@ -79,12 +112,40 @@ __host__ __device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uin
 struct Acc128 {
     uint64_t lo, hi;
 };
+// acc += a b (mod 2^128). On the device the four 32 x 32-bit partial products
+// are accumulated straight into the four 32-bit words of acc with carry chains
+// (schoolbook multiplication): no separate 64-bit high and low products, which
+// would each recompute the cross terms.
 __host__ __device__ __forceinline__ void mac(Acc128 &acc, uint64_t a, uint64_t b)
 {
+#ifdef __CUDA_ARCH__
+    asm("{\n\t"
+        ".reg .u32 a0, a1, b0, b1, w0, w1, w2, w3;\n\t"
+        "mov.b64 {a0, a1}, %2;\n\t"
+        "mov.b64 {b0, b1}, %3;\n\t"
+        "mov.b64 {w0, w1}, %0;\n\t"
+        "mov.b64 {w2, w3}, %1;\n\t"
+        "mad.lo.cc.u32 w0, a0, b0, w0;\n\t"   // + a0 b0 + a1 b1 2^64
+        "madc.hi.cc.u32 w1, a0, b0, w1;\n\t"
+        "madc.lo.cc.u32 w2, a1, b1, w2;\n\t"
+        "madc.hi.u32 w3, a1, b1, w3;\n\t"
+        "mad.lo.cc.u32 w1, a0, b1, w1;\n\t"   // + a0 b1 2^32
+        "madc.hi.cc.u32 w2, a0, b1, w2;\n\t"
+        "addc.u32 w3, w3, 0;\n\t"
+        "mad.lo.cc.u32 w1, a1, b0, w1;\n\t"   // + a1 b0 2^32
+        "madc.hi.cc.u32 w2, a1, b0, w2;\n\t"
+        "addc.u32 w3, w3, 0;\n\t"
+        "mov.b64 %0, {w0, w1};\n\t"
+        "mov.b64 %1, {w2, w3};\n\t"
+        "}"
+        : "+l"(acc.lo), "+l"(acc.hi)
+        : "l"(a), "l"(b));
+#else
     uint64_t l = a * b;
     uint64_t h = mulhi64(a, b);
     acc.lo += l;
     acc.hi += h + (acc.lo < l);
+#endif
 }
 
 // ---------------------------------------------------------------------------
