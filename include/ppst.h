@@ -124,6 +124,12 @@ const char *ppst_last_error(const ppst_ctx *ctx);
  * transform chunks each block owns, 4, 8 (default) or 16 (PPST_E_ARG
  * otherwise). Changes speed only, never results; the autotuner measures it. */
 int ppst_ctx_set_tile(ppst_ctx *ctx, uint32_t inner_sub);
+/* Block shape of the transform passes (no counterpart in the paper): a pass
+ * over few limbs runs 8 or 4 sub-transforms per block instead of 16 (and the
+ * inner product a smaller tile than ppst_ctx_set_tile's) whenever 16 would give
+ * a grid of fewer than `min_blocks` blocks (default 456 = 3 x 152 SMs; 0: always
+ * 16; 2^20: always 4). Changes speed only, never results. PPST_E_ARG above 2^20. */
+int ppst_ctx_set_pass_blocks(ppst_ctx *ctx, uint32_t min_blocks);
 /* Failure-detection self-test (no counterpart in the paper): launches one block
  * that waits on a shared-memory barrier nothing completes, bounded by timeout_us
  * (1 .. 10^6); like the kernels with asynchronous copies, it records the timeout

@@ -443,6 +443,10 @@ class Context:
         self._check(lib.ppst_ctx_set_tile(self.ptr, int(inner_sub)))
         self.inner_sub = int(inner_sub)
 
+
+    def set_pass_blocks(self, min_blocks):
+        """ppst_ctx_set_pass_blocks: smaller transform blocks below this grid size (speed only)."""
+        self._check(lib.ppst_ctx_set_pass_blocks(self.ptr, int(min_blocks)))
     def selftest_wait(self, timeout_us):
         """Launch a kernel whose bounded wait times out (failure-detection test);
         the next synchronising call raises PpstError(PPST_E_CUDA)."""

@@ -78,6 +78,7 @@ SIGNATURES = {
     "ppst_rotsum": (c_int, [c_void_p, c_void_p, c_void_p, PP]),
     "ppst_selftest_wait": (c_int, [c_void_p, c_u32]),
     "ppst_ctx_set_tile": (c_int, [c_void_p, c_u32]),
+    "ppst_ctx_set_pass_blocks": (c_int, [c_void_p, c_u32]),
     "ppst_inv_sqrt": (c_int, [c_void_p, c_void_p, c_void_p, c_double, ctypes.c_int32, ctypes.c_int32, PP]),
     "ppst_rescale": (c_int, [c_void_p, c_void_p, PP]),
     "ppst_add": (c_int, [c_void_p, c_void_p, c_void_p, PP]),

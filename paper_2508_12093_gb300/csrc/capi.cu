@@ -103,6 +103,16 @@ int ppst_ctx_set_tile(ppst_ctx *ctx, uint32_t inner_sub)
     });
 }
 
+int ppst_ctx_set_pass_blocks(ppst_ctx *ctx, uint32_t min_blocks)
+{
+    Ctx *c = (Ctx *)ctx;
+    if (!ok(c, TAG_CTX)) return PPST_E_ARG;
+    return guard(c, [&] {
+        REQ(min_blocks <= (1u << 20), "min_blocks out of range [0, 2^20]");
+        c->pass_min_blocks = min_blocks;
+    });
+}
+
 int ppst_selftest_wait(ppst_ctx *ctx, uint32_t timeout_us)
 {
     Ctx *c = (Ctx *)ctx;

@@ -125,6 +125,7 @@ struct Prof {
 
 struct Ctx {
     uint32_t tag = TAG_CTX;
+    uint32_t pass_min_blocks = 456;  // transform passes: smaller blocks below this grid size (3 x 152 SMs)
     Prof prof;
     ppst_params prm{};
     int logN = 0, N = 0, S = 0, L = 0, K = 0, dnum = 0, alpha = 0, np = 0;

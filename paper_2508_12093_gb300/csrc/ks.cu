@@ -28,31 +28,9 @@
 // through each stage in one launch. The item is the fastest-varying block
 // index of the inner-product kernel, so the blocks that read the same key
 // tile run back to back and the tile is fetched from HBM once per batch.
-#include <atomic>
-
-#include "bulk.cuh"
-#include "ntt.cuh"
+#include "ks.cuh"
 
 namespace ppst {
-
-constexpr int BMAX = 16;
-
-// per-item ciphertext pointers of a batched launch
-struct ItemPtrs {
-    const uint64_t *in0[BMAX];
-    const uint64_t *in1[BMAX];
-    uint64_t *out[BMAX];
-};
-
-// workspace slices of item `it`
-struct Ws {
-    size_t d2, ext, acc, conv, top;  // item strides in words
-};
-static inline Ws ws_strides(const Ctx &c)
-{
-    const size_t N = c.N, q = c.L + 1, e = c.ext_rows();
-    return Ws{q * N, (size_t)c.dnum * e * N, 2 * e * N, 2 * q * N, 2 * N};
-}
 
 // ---------------------------------------------------------------------------
 // 0. batched tensor / automorphism into the key-switch input buffers
@@ -63,18 +41,18 @@ static inline Ws ws_strides(const Ctx &c)
 // owns SUB chunks of one limb, so each thread's E words (stored at h + T k,
 // natural E h + k) are exactly what the inverse CHUNKS pass takes; d2 leaves in
 // that pass's output layout for the COLS pass.
-template <int S>
-__global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS)
+template <int S, int SUB>
+__global__ void __launch_bounds__(PassShape<S, SUB>::THREADS, PassShape<S, SUB>::MIN_BLOCKS)
     k_tensor_ic(ItemPtrs ip, uint64_t *__restrict__ d2, uint64_t *__restrict__ d2n, const PrimeC *__restrict__ pc,
                 const Tw *__restrict__ twi, int logN, int nl, size_t pstride, size_t d2_stride)
 {
-    typedef PassShape<S> P;
+    typedef PassShape<S, SUB> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN;
     const int it = blockIdx.y / nl, i = blockIdx.y - it * nl;
     const PrimeC p = pc[i];
     int h, sub;
-    pass_coords<S, false>(h, sub);
+    pass_coords<S, false, SUB>(h, sub);
     const int g = blockIdx.x * P::SUB + sub;
     const size_t base = (size_t)i * N + (size_t)g * P::M + h;
     const uint64_t *a = ip.in0[it], *b = ip.in1[it];
@@ -99,17 +77,17 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCK
 }
 
 // blockIdx.y = (item, poly, limb): poly 0 -> out[item].c0, poly 1 -> d2n and (after the pass) d2
-template <int S>
-__global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS)
+template <int S, int SUB>
+__global__ void __launch_bounds__(PassShape<S, SUB>::THREADS, PassShape<S, SUB>::MIN_BLOCKS)
     k_automorph_ic(ItemPtrs ip, uint64_t *__restrict__ d2, uint64_t *__restrict__ d2n, const PrimeC *__restrict__ pc,
                    const Tw *__restrict__ twi, int logN, int nl, uint64_t gal, size_t pstride, size_t d2_stride)
 {
-    typedef PassShape<S> P;
+    typedef PassShape<S, SUB> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN;
     const int row = blockIdx.y, it = row / (2 * nl), r2 = row - it * 2 * nl, poly = r2 / nl, i = r2 - poly * nl;
     int h, sub;
-    pass_coords<S, false>(h, sub);
+    pass_coords<S, false, SUB>(h, sub);
     const int g = blockIdx.x * P::SUB + sub;
     const size_t o = (size_t)i * N;
     const uint64_t *src = ip.in0[it] + (size_t)poly * pstride + o;
@@ -136,61 +114,13 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCK
     for (int k = 0; k < P::E; k++) d2[it * d2_stride + base + P::T * k] = x[k];
 }
 
-// ---------------------------------------------------------------------------
-// 2. ModUp fused into the COLS pass
-// ---------------------------------------------------------------------------
-// sum_{i < A} src[i N + pos] f[i] mod q for the E words of this thread (A known at
-// compile time: fully unrolled, all loads independent); A = 0: runtime count `a`
-template <int A, int E, int T>
-__device__ __forceinline__ void bconv_words(uint64_t (&x)[E], const uint64_t *__restrict__ src, const uint64_t *f,
-                                            int a, int N, int C, int h, const PrimeC &pt)
-{
-    if (A > 0) {
-        uint64_t fr[A > 0 ? A : 1];
-#pragma unroll
-        for (int i = 0; i < A; i++) fr[i] = f[i];
-#pragma unroll
-        for (int k = 0; k < E; k++) {
-            const size_t pos = (size_t)(h + T * k) * C;
-            Acc128 acc{0, 0};
-#pragma unroll
-            for (int i = 0; i < A; i++) mac(acc, src[(size_t)i * N + pos], fr[i]);
-            x[k] = mont_redc(acc.hi, acc.lo, pt.q, pt.qinv);
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < E; k++) {
-            const size_t pos = (size_t)(h + T * k) * C;
-            Acc128 acc{0, 0};
-#pragma unroll 1
-            for (int i = 0; i < a; i++) mac(acc, src[(size_t)i * N + pos], f[i]);
-            x[k] = mont_redc(acc.hi, acc.lo, pt.q, pt.qinv);
-        }
-    }
-}
-
-// calls f(std::integral_constant<int, a>) for the digit sizes with a compiled fast path, else f(0)
-template <class F>
-void dispatch_a(int a, F &&f)
-{
-    switch (a) {
-    case 1: f(std::integral_constant<int, 1>{}); break;
-    case 2: f(std::integral_constant<int, 2>{}); break;
-    case 3: f(std::integral_constant<int, 3>{}); break;
-    case 4: f(std::integral_constant<int, 4>{}); break;
-    case 6: f(std::integral_constant<int, 6>{}); break;
-    case 8: f(std::integral_constant<int, 8>{}); break;
-    default: f(std::integral_constant<int, 0>{}); break;
-    }
-}
-
-template <int S, int ALPHA>
-__global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
+template <int S, int ALPHA, int SUB>
+__global__ void __launch_bounds__(PassShape<S, SUB>::THREADS, 2)
     k_modup_cols(const uint64_t *__restrict__ y, uint64_t *__restrict__ ext, const uint64_t *__restrict__ ks,
                  DigitOffs offs, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN, int level,
                  int alpha, int L, int K, int nd, size_t ext_stride, Ws ws)
 {
-    typedef PassShape<S> P;
+    typedef PassShape<S, SUB> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN, C = N >> S;
     const int E_ext = level + 1 + K;
@@ -205,13 +135,13 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
     if (threadIdx.x < a) f[threadIdx.x] = ks[offs.off[j] + 2 * a + (size_t)threadIdx.x * E_ext + e];
     __syncthreads();
     int h, sub;
-    pass_coords<S, true>(h, sub);
+    pass_coords<S, true, SUB>(h, sub);
     const int g = blockIdx.x * P::SUB + sub;
     uint64_t x[P::E];
     const uint64_t *yl = y + it * ws.d2 + (size_t)lo * N + g;
     if (ALPHA > 0 && a == ALPHA) bconv_words<ALPHA, P::E, P::T>(x, yl, f, a, N, C, h, pt);
     else bconv_words<0, P::E, P::T>(x, yl, f, a, N, C, h, pt);  // a partial last digit
-    cols_fwd_core<S>(x, sm, h, sub, tw + (size_t)t * N, pt.q);
+    cols_fwd_core<S, SUB>(x, sm, h, sub, tw + (size_t)t * N, pt.q);
     uint64_t *out = ext + it * ws.ext + (size_t)j * ext_stride + (size_t)e * N;
 #pragma unroll
     for (int k = 0; k < P::E; k++) out[(size_t)(P::E * h + k) * C + g] = x[k];
@@ -245,7 +175,7 @@ __global__ void __launch_bounds__(InnerSmem<S, SUB>::THREADS, InnerSmem<S, SUB>:
                    uint64_t *__restrict__ acc, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN,
                    int level, int alpha, int L, int K, int nd, size_t ext_stride, int B, Ws ws, int *err)
 {
-    typedef PassShape<S> P;
+    typedef PassShape<S, SUB> P;
     typedef InnerSmem<S, SUB> SM;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);  // [0], [1]: digit stages; [2]: key stage
@@ -287,7 +217,7 @@ __global__ void __launch_bounds__(InnerSmem<S, SUB>::THREADS, InnerSmem<S, SUB>:
     }
     __syncthreads();
     int h, sub;
-    pass_coords<S, false>(h, sub);
+    pass_coords<S, false, SUB>(h, sub);
     const int g = tile * SM::SUB + sub;
     const int w0 = sub * P::M + h;  // this thread's words of a tile: w0 + T k
     uint64_t a0[P::E], a1[P::E];
@@ -336,294 +266,6 @@ __global__ void __launch_bounds__(InnerSmem<S, SUB>::THREADS, InnerSmem<S, SUB>:
 }
 
 // ---------------------------------------------------------------------------
-// ModDown (+ rescale)
-// ---------------------------------------------------------------------------
-// u_k = d_k[l] + acc_k[l] P^-1 (evaluation domain), the top limb before its inverse transform
-__global__ void k_md_top_kernel(ItemPtrs ip, uint64_t *__restrict__ acc, const PrimeC *__restrict__ pc, Tw pinv,
-                                int N, int level, size_t pstride, size_t ext_stride, Ws ws)
-{
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
-    const int it = blockIdx.y / 2, k = blockIdx.y - 2 * it;
-    const uint64_t q = pc[level].q;
-    const size_t o = (size_t)level * N + c;
-    uint64_t *a = acc + it * ws.acc + (size_t)k * ext_stride + o;
-    const uint64_t v = csub(shoup(*a, pinv.w, pinv.s, q), q);
-    *a = add_mod(ip.in0[it][(size_t)k * pstride + o], v, q);  // in place: row l of acc_k is not needed otherwise
-}
-
-// top_k = INTT(u_k) - conv_l(y_k) P^-1 (coefficient domain): INTT(u_k) is row l of acc_k, y_k its P rows
-// after ModDown's first factor
-__global__ void k_md_topfix_kernel(const uint64_t *__restrict__ acc, uint64_t *__restrict__ top,
-                                   const uint64_t *__restrict__ hMP, const PrimeC *__restrict__ pc, Tw pinv, int N,
-                                   int level, int L, int K, size_t ext_stride, Ws ws)
-{
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
-    const int it = blockIdx.y / 2, k = blockIdx.y - 2 * it;
-    const PrimeC p = pc[level];
-    const uint64_t *ym = acc + it * ws.acc + (size_t)k * ext_stride + (size_t)(level + 1) * N + c;
-    Acc128 a{0, 0};
-    for (int m = 0; m < K; m++) mac(a, ym[(size_t)m * N], hMP[(size_t)m * (L + 1) + level]);
-    const uint64_t conv = mont_redc(a.hi, a.lo, p.q, p.qinv);
-    const uint64_t v = csub(shoup(conv, pinv.w, pinv.s, p.q), p.q);
-    const uint64_t u = acc[it * ws.acc + (size_t)k * ext_stride + (size_t)level * N + c];
-    top[it * ws.top + (size_t)k * N + c] = sub_mod(u, v, p.q);
-}
-
-// COLS pass of z_i = conv_i(y) P^-1 (+ [top]_centred mod q_i when rescaling), limbs i < nl of both polys
-template <int S, bool RESC, int KT>
-__global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
-    k_md_cols(const uint64_t *__restrict__ acc, const uint64_t *__restrict__ top, uint64_t *__restrict__ z,
-              const uint64_t *__restrict__ hMP, const MdC *__restrict__ mdc, const PrimeC *__restrict__ pc,
-              const Tw *__restrict__ tw, int logN, int level, int nl, int L, int K, size_t ext_stride,
-              size_t z_stride, Ws ws)
-{
-    typedef PassShape<S> P;
-    __shared__ uint64_t sm[P::SMEM_WORDS];
-    const int N = 1 << logN, C = N >> S;
-    const int it = blockIdx.y / (2 * nl), rem = blockIdx.y - it * 2 * nl;
-    const int k = rem / nl, i = rem - k * nl;
-    const PrimeC p = pc[i];
-    const MdC mc = mdc[i];
-    __shared__ uint64_t f[16];
-    if (threadIdx.x < K) f[threadIdx.x] = hMP[(size_t)threadIdx.x * (L + 1) + i];
-    __syncthreads();
-    const uint64_t ql = pc[level].q;
-    int h, sub;
-    pass_coords<S, true>(h, sub);
-    const int g = blockIdx.x * P::SUB + sub;
-    const uint64_t *ym = acc + it * ws.acc + (size_t)k * ext_stride + (size_t)(level + 1) * N + g;
-    const uint64_t *tk = top + it * ws.top + (size_t)k * N + g;
-    uint64_t x[P::E];
-    bconv_words<KT, P::E, P::T>(x, ym, f, K, N, C, h, p);
-#pragma unroll
-    for (int kk = 0; kk < P::E; kk++) {
-        uint64_t v = csub(shoup(x[kk], mc.pinv.w, mc.pinv.s, p.q), p.q);
-        if (RESC) {
-            const uint64_t tv = tk[(size_t)(h + P::T * kk) * C];
-            uint64_t r = csub(shoup(tv, 1, p.w64, p.q), p.q);
-            if (tv > (ql >> 1)) r = sub_mod(r, mc.qmod, p.q);
-            v = add_mod(v, r, p.q);
-        }
-        x[kk] = v;
-    }
-    cols_fwd_core<S>(x, sm, h, sub, tw + (size_t)i * N, p.q);
-    uint64_t *out = z + it * ws.conv + (size_t)k * z_stride + (size_t)i * N;
-#pragma unroll
-    for (int kk = 0; kk < P::E; kk++) out[(size_t)(P::E * h + kk) * C + g] = x[kk];
-}
-
-// CHUNKS pass of z and the output combine:
-//   RESC:  out_i = d_i q_l^-1 + acc_i (P^-1 q_l^-1) - Z_i q_l^-1     (d = in0[item])
-//   else:  out_i = add_i + acc_i P^-1 - Z_i        (add = in0[item] for c0, 0 for c1)
-// The block's acc and d tiles (contiguous SUB M words each) are fetched by bulk
-// asynchronous copies issued at the start, so they arrive while z is transformed.
-template <int S>
-struct MdSmem {
-    typedef PassShape<S> P;
-    static constexpr int TILE = P::SUB * P::M;
-    static constexpr size_t A_OFF = 128;                           // acc tile
-    static constexpr size_t D_OFF = A_OFF + (size_t)TILE * 8;      // d tile
-    static constexpr size_t T_OFF = D_OFF + (size_t)TILE * 8;      // transpose buffer
-    static constexpr size_t BYTES = T_OFF + (size_t)P::SMEM_WORDS * 8;
-};
-
-template <int S, bool RESC>
-__global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
-    k_md_chunks(const uint64_t *__restrict__ z, const uint64_t *__restrict__ acc, ItemPtrs ip,
-                const MdC *__restrict__ mdc, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN, int nl,
-                size_t ext_stride, size_t z_stride, size_t pstride, Ws ws, int *err)
-{
-    typedef PassShape<S> P;
-    typedef MdSmem<S> SM;
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    const uint64_t *at = reinterpret_cast<const uint64_t *>(smem + SM::A_OFF);
-    const uint64_t *dt = reinterpret_cast<const uint64_t *>(smem + SM::D_OFF);
-    uint64_t *sm = reinterpret_cast<uint64_t *>(smem + SM::T_OFF);
-    constexpr uint32_t TB = SM::TILE * 8;
-    const int N = 1 << logN;
-    const int it = blockIdx.y / (2 * nl), rem = blockIdx.y - it * 2 * nl;
-    const int k = rem / nl, i = rem - k * nl;
-    const PrimeC p = pc[i];
-    const MdC mc = mdc[i];
-    const size_t t0 = (size_t)i * N + (size_t)blockIdx.x * SM::TILE;  // the block's tile in a polynomial
-    const uint64_t *ad = (RESC || k == 0) ? ip.in0[it] + (size_t)k * pstride : nullptr;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_fence_init();
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bar[0], ad ? 2 * TB : TB);
-        bulk_g2s(smem + SM::A_OFF, acc + it * ws.acc + (size_t)k * ext_stride + t0, TB, &bar[0]);
-        if (ad) bulk_g2s(smem + SM::D_OFF, ad + t0, TB, &bar[0]);
-    }
-    __syncthreads();
-    int h, sub;
-    pass_coords<S, false>(h, sub);
-    const int g = blockIdx.x * P::SUB + sub;
-    const int w0 = sub * P::M + h;  // this thread's words of a tile: w0 + T kk (natural E h + kk)
-    uint64_t x[P::E];
-    const uint64_t *src = z + it * ws.conv + (size_t)k * z_stride + t0 + w0;
-#pragma unroll
-    for (int kk = 0; kk < P::E; kk++) x[kk] = src[P::T * kk];
-    chunks_fwd_core<S>(x, sm, h, sub, g, N, tw + (size_t)i * N, p.q);
-    if (__syncthreads_or(!mbar_wait(&bar[0], 0))) {  // the tiles did not arrive in time
-        if (threadIdx.x == 0) {
-            *(volatile int *)err = 1;
-            mbar_wait(&bar[0], 0);
-        }
-        return;
-    }
-    uint64_t *od = ip.out[it] + (size_t)k * pstride + t0 + w0;
-#pragma unroll
-    for (int kk = 0; kk < P::E; kk++) {
-        const uint64_t Z = reduce4q(x[kk], p.q);
-        const uint64_t av = at[w0 + P::T * kk];
-        uint64_t r;
-        if (RESC) {
-            const uint64_t dv = dt[w0 + P::T * kk];
-            r = csub(shoup(dv, mc.qlinv.w, mc.qlinv.s, p.q), p.q);
-            r = add_mod(r, csub(shoup(av, mc.pq.w, mc.pq.s, p.q), p.q), p.q);
-            r = sub_mod(r, csub(shoup(Z, mc.qlinv.w, mc.qlinv.s, p.q), p.q), p.q);
-        } else {
-            r = csub(shoup(av, mc.pinv.w, mc.pinv.s, p.q), p.q);
-            if (ad) r = add_mod(r, dt[w0 + P::T * kk], p.q);
-            r = sub_mod(r, Z, p.q);
-        }
-        od[P::T * kk] = r;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// host orchestration
-// ---------------------------------------------------------------------------
-static dim3 grid_s(const Ctx &c, int S, int rows) { return dim3((c.N >> S) / 16, rows); }
-
-// ---------------------------------------------------------------------------
-// rescale after Mul(P) (Sec. 3.1 levels): out_i = c_i m_i q_l^-1 - NTT([c_l]_centred mod q_i) q_l^-1
-// ---------------------------------------------------------------------------
-// COLS pass of [top]_centred mod q_i (top = limb l in the coefficient domain, L2-resident)
-template <int S>
-__global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
-    k_resc_cols(const uint64_t *__restrict__ top, uint64_t *__restrict__ z, const PrimeC *__restrict__ pc,
-                ConstVec qmod, const Tw *__restrict__ tw, int logN, int level, size_t z_stride)
-{
-    typedef PassShape<S> P;
-    __shared__ uint64_t sm[P::SMEM_WORDS];
-    const int N = 1 << logN, C = N >> S;
-    const int k = blockIdx.y / level, i = blockIdx.y - k * level;
-    const PrimeC p = pc[i];
-    const uint64_t ql = pc[level].q;
-    int h, sub;
-    pass_coords<S, true>(h, sub);
-    const int g = blockIdx.x * P::SUB + sub;
-    const uint64_t *tk = top + (size_t)k * N + g;
-    uint64_t x[P::E];
-#pragma unroll
-    for (int kk = 0; kk < P::E; kk++) {
-        const uint64_t v = tk[(size_t)(h + P::T * kk) * C];
-        uint64_t r = csub(shoup(v, 1, p.w64, p.q), p.q);  // v mod q_i
-        if (v > (ql >> 1)) r = sub_mod(r, qmod.c[i], p.q);  // centred: v - q_l
-        x[kk] = r;
-    }
-    cols_fwd_core<S>(x, sm, h, sub, tw + (size_t)i * N, p.q);
-    uint64_t *out = z + (size_t)k * z_stride + (size_t)i * N;
-#pragma unroll
-    for (int kk = 0; kk < P::E; kk++) out[(size_t)(P::E * h + kk) * C + g] = x[kk];
-}
-
-// CHUNKS pass of z and the combine; the block's tile of c is fetched by a bulk
-// asynchronous copy while z is transformed
-template <int S>
-struct RescSmem {
-    typedef PassShape<S> P;
-    static constexpr int TILE = P::SUB * P::M;
-    static constexpr size_t A_OFF = 128;
-    static constexpr size_t T_OFF = A_OFF + (size_t)TILE * 8;
-    static constexpr size_t BYTES = T_OFF + (size_t)P::SMEM_WORDS * 8;
-};
-
-template <int S>
-__global__ void __launch_bounds__(PassShape<S>::THREADS, 2)
-    k_resc_chunks(const uint64_t *__restrict__ z, const uint64_t *__restrict__ a, uint64_t *__restrict__ out,
-                  const PrimeC *__restrict__ pc, ConstVec qlinv, ConstVec mq, const Tw *__restrict__ tw, int logN,
-                  int level, size_t z_stride, size_t pstride, int *err)
-{
-    typedef PassShape<S> P;
-    typedef RescSmem<S> SM;
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    const uint64_t *at = reinterpret_cast<const uint64_t *>(smem + SM::A_OFF);
-    uint64_t *sm = reinterpret_cast<uint64_t *>(smem + SM::T_OFF);
-    const int N = 1 << logN;
-    const int k = blockIdx.y / level, i = blockIdx.y - k * level;
-    const uint64_t q = pc[i].q;
-    const size_t t0 = (size_t)i * N + (size_t)blockIdx.x * SM::TILE;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_fence_init();
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bar[0], SM::TILE * 8);
-        bulk_g2s(smem + SM::A_OFF, a + (size_t)k * pstride + t0, SM::TILE * 8, &bar[0]);
-    }
-    __syncthreads();
-    int h, sub;
-    pass_coords<S, false>(h, sub);
-    const int g = blockIdx.x * P::SUB + sub;
-    const int w0 = sub * P::M + h;
-    uint64_t x[P::E];
-    const uint64_t *src = z + (size_t)k * z_stride + t0 + w0;
-#pragma unroll
-    for (int kk = 0; kk < P::E; kk++) x[kk] = src[P::T * kk];
-    chunks_fwd_core<S>(x, sm, h, sub, g, N, tw + (size_t)i * N, q);
-    if (__syncthreads_or(!mbar_wait(&bar[0], 0))) {  // the tile did not arrive in time
-        if (threadIdx.x == 0) {
-            *(volatile int *)err = 1;
-            mbar_wait(&bar[0], 0);
-        }
-        return;
-    }
-    uint64_t *od = out + (size_t)k * pstride + t0 + w0;
-#pragma unroll
-    for (int kk = 0; kk < P::E; kk++) {
-        const uint64_t Z = reduce4q(x[kk], q);
-        const uint64_t xv = csub(shoup(at[w0 + P::T * kk], mq.c[i], mq.sh[i], q), q);
-        const uint64_t yv = csub(shoup(Z, qlinv.c[i], qlinv.sh[i], q), q);
-        od[P::T * kk] = sub_mod(xv, yv, q);
-    }
-}
-
-// top: limb l of both polynomials in the coefficient domain ([2][N]); z: scratch [2][L+1][N]
-void ks_rescale(Ctx &c, const CtObj &a, const uint64_t *top, uint64_t *z, const ConstVec &mq, CtObj &out)
-{
-    const int l = a.level;
-    const size_t ps = (size_t)(c.L + 1) * c.N;
-    {
-        ProfScope _ps(c, "rescale_cols", (uint64_t)2 * l + 2);
-        dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
-            constexpr int S = decltype(sv)::value;
-            launch_on(c, k_resc_cols<S>, grid_s(c, S, 2 * l), PassShape<S>::THREADS, 0, top, z, c.d_pc,
-                c.resc_qmodv[l], c.d_twf, c.logN, l, ps);
-        });
-        check_launch("k_resc_cols");
-    }
-    ProfScope _ps(c, "rescale_chunks", (uint64_t)6 * l);
-    dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
-        constexpr int S = decltype(sv)::value;
-        const size_t smem = RescSmem<S>::BYTES;
-        static std::atomic<bool> attr_set{false};
-        if (!attr_set.load()) {
-            PPST_CUDA(cudaFuncSetAttribute(k_resc_chunks<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr_set = true;
-        }
-        launch_on(c, k_resc_chunks<S>, grid_s(c, S, 2 * l), PassShape<S>::THREADS, smem, z, a.d, out.d, c.d_pc,
-            c.resc[l], mq, c.d_twf, c.logN, l, ps, ps, c.d_err);
-    });
-    check_launch("k_resc_chunks");
-}
-
-// ---------------------------------------------------------------------------
 // failure-detection self-test: one block waits on a barrier whose phase never
 // completes (nothing is copied), gives up after limit_ns, records the timeout in
 // the error word and returns, exactly as the pipelined kernels do
@@ -663,12 +305,13 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
         uint64_t targets = 0;
         for (int j = 0; j < nd; j++) targets += E_ext - (std::min((j + 1) * c.alpha, level + 1) - j * c.alpha);
         ProfScope _ps(c, "modup_cols", (uint64_t)B * ((level + 1) + targets));  // limbs read once + written
-        dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
-            constexpr int S = decltype(sv)::value;
+        dispatch_pass(c, ntt_s_rows(c.logN), (int)targets * B, [&](auto sv, auto bv) {
+            constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
             dispatch_a(c.alpha, [&](auto av) {
                 constexpr int A = decltype(av)::value;
-                launch_on(c, k_modup_cols<S, A>, grid_s(c, S, B * nd * E_ext), PassShape<S>::THREADS, 0, c.ws_d2,
-                    c.ws_ext, c.d_ks, offs, c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, ws);
+                launch_on(c, k_modup_cols<S, A, SUB>, grid_s(c, S, SUB, B * nd * E_ext), PassShape<S, SUB>::THREADS,
+                    0, c.ws_d2, c.ws_ext, c.d_ks, offs, c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es,
+                    ws);
             });
         });
         check_launch("k_modup_cols");
@@ -691,74 +334,17 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
             c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, B, ws, c.d_err);
     };
     dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
-        switch (c.inner_sub) {
+        constexpr int S = decltype(sv)::value;
+        // the context's tile, halved (down to 4 chunks) while the grid would leave SMs idle
+        int tile = c.inner_sub;
+        while (tile > 4 && (long)B * ((c.N >> S) / tile) * E_ext < (long)c.pass_min_blocks) tile /= 2;
+        switch (tile) {
         case 4: launch(sv, std::integral_constant<int, 4>{}); break;
         case 16: launch(sv, std::integral_constant<int, 16>{}); break;
         default: launch(sv, std::integral_constant<int, 8>{}); break;
         }
     });
     check_launch("k_inner_chunks");
-}
-
-// ModDown of ws_acc (+ rescale) for B items. RESC: out[b] (level-1) =
-// rescale(in0[b] + ModDown(acc[b])), in0 = the tensor product; else out[b].c0 =
-// in0[b] + ModDown(acc_0), out[b].c1 = ModDown(acc_1).
-template <bool RESC>
-static void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip)
-{
-    const Ws ws = ws_strides(c);
-    const size_t es = c.ext_rows() * c.N, ps = (size_t)(c.L + 1) * c.N;
-    const int nl = RESC ? level : level + 1;
-    const MdC *mdc = c.d_md_const + (size_t)level * (c.L + 1);
-    const MdC &hm = c.md_const[(size_t)level * (c.L + 1) + level];
-    const dim3 eg(c.N / 256, 2 * B);
-    if (RESC) {
-        ProfScope _ps(c, "moddown_top", (uint64_t)6 * B);
-        launch_on(c, k_md_top_kernel, eg, 256, 0, ip, c.ws_acc, c.d_pc, hm.pinv, c.N, level, ps, es, ws);
-        check_launch("k_md_top");
-        // rows l .. l + K of both accumulators of every item (the top limb u_k, then
-        // the P rows) to the coefficient domain in one transform: row l times N^-1,
-        // P row m times N^-1 (P / p_m)^-1
-        LimbMap mp{c.ws_acc + (size_t)level * c.N, es, c.K + 1, 2 * B, 1, level, c.L + 1};
-        ntt_inv_mul(c, mp, c.d_md_outmul_top + (size_t)level * (c.K + 1));
-    } else {
-        // P rows of both accumulators of every item to the coefficient domain, times (P / p_m)^-1
-        LimbMap mp{c.ws_acc + (size_t)(level + 1) * c.N, es, c.K, 2 * B, 0, 0, c.L + 1};
-        ntt_inv_mul(c, mp, c.d_md_outmul);
-    }
-    const uint64_t *hMP = c.d_ks + c.moddown_off + 2 * c.K;
-    if (RESC) {
-        ProfScope _ps(c, "moddown_top", (uint64_t)B * (2 * c.K + 4));
-        launch_on(c, k_md_topfix_kernel, eg, 256, 0, c.ws_acc, c.ws_top, hMP, c.d_pc, hm.pinv, c.N, level, c.L, c.K,
-                                                      es, ws);
-        check_launch("k_md_topfix");
-    }
-    {
-        ProfScope _ps(c, "moddown_cols", (uint64_t)B * (2 * c.K + (RESC ? 2 : 0) + 2 * nl));
-        dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
-            constexpr int S = decltype(sv)::value;
-            dispatch_a(c.K, [&](auto kv) {
-                constexpr int KT = decltype(kv)::value;
-                launch_on(c, k_md_cols<S, RESC, KT>, grid_s(c, S, B * 2 * nl), PassShape<S>::THREADS, 0, c.ws_acc,
-                    c.ws_top, c.ws_conv, hMP, mdc, c.d_pc, c.d_twf, c.logN, level, nl, c.L, c.K, es, ps, ws);
-            });
-        });
-        check_launch("k_md_cols");
-    }
-    ProfScope _ps(c, "moddown_chunks", (uint64_t)B * (RESC ? 8 : 7) * nl);
-    dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
-        constexpr int S = decltype(sv)::value;
-        const size_t smem = MdSmem<S>::BYTES;
-        static std::atomic<bool> attr_set{false};
-        if (!attr_set.load()) {
-            PPST_CUDA(cudaFuncSetAttribute(k_md_chunks<S, RESC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-            attr_set = true;
-        }
-        launch_on(c, k_md_chunks<S, RESC>, grid_s(c, S, B * 2 * nl), PassShape<S>::THREADS, smem, c.ws_conv,
-            c.ws_acc, ip, mdc, c.d_pc, c.d_twf, c.logN, nl, es, ps, ps, ws, c.d_err);
-    });
-    check_launch("k_md_chunks");
 }
 
 // HMult of B pairs (each pair at its own min level; all pairs share that level):
@@ -787,10 +373,10 @@ std::vector<CtObj *> ev_hmult_batch(Ctx &c, const EvkObj &k, const std::vector<c
         }
         {
             ProfScope _ps(c, "tensor", (uint64_t)B * 7 * (lv + 1));
-            dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
-                constexpr int S = decltype(sv)::value;
-                launch_on(c, k_tensor_ic<S>, dim3((c.N >> S) / PassShape<S>::SUB, B * (lv + 1)),
-                    PassShape<S>::THREADS, 0, ip, c.ws_d2, c.ws_d2n, c.d_pc, c.d_twi, c.logN, lv + 1, ps, ws.d2);
+            dispatch_pass(c, ntt_s_chunk(c.logN), B * (lv + 1), [&](auto sv, auto bv) {
+                constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
+                launch_on(c, k_tensor_ic<S, SUB>, grid_s(c, S, SUB, B * (lv + 1)), PassShape<S, SUB>::THREADS, 0,
+                    ip, c.ws_d2, c.ws_d2n, c.d_pc, c.d_twi, c.logN, lv + 1, ps, ws.d2);
             });
             check_launch("k_tensor_ic");
         }
@@ -844,10 +430,10 @@ std::vector<CtObj *> ev_rotate_batch(Ctx &c, const EvkObj &k, const std::vector<
         }
         {
             ProfScope _ps(c, "automorph", (uint64_t)B * 5 * (lv + 1));
-            dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
-                constexpr int S = decltype(sv)::value;
-                launch_on(c, k_automorph_ic<S>, dim3((c.N >> S) / PassShape<S>::SUB, B * 2 * (lv + 1)),
-                    PassShape<S>::THREADS, 0, ip, c.ws_d2, c.ws_d2n, c.d_pc, c.d_twi, c.logN, lv + 1,
+            dispatch_pass(c, ntt_s_chunk(c.logN), B * (lv + 1), [&](auto sv, auto bv) {
+                constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
+                launch_on(c, k_automorph_ic<S, SUB>, grid_s(c, S, SUB, B * 2 * (lv + 1)),
+                    PassShape<S, SUB>::THREADS, 0, ip, c.ws_d2, c.ws_d2n, c.d_pc, c.d_twi, c.logN, lv + 1,
                     galois_elt(c, rr), ps, ws.d2);
             });
             check_launch("k_automorph_ic");

@@ -12,44 +12,45 @@
 //   COLS pass   the log2 R stages of distance >= C: every column
 //               (c, c + C, c + 2C, ...) is an independent R-point transform;
 //   CHUNKS pass the remaining stages, inside contiguous chunks of C words.
-// A block runs 16 sub-transforms (16 columns = 128-byte rows, or 16 chunks);
-// the per-thread register scheme is in ntt.cuh.
+// A block runs SUB sub-transforms (SUB columns or chunks; 16 for large grids,
+// 8 or 4 when few limbs would leave SMs idle); the per-thread register scheme
+// is in ntt.cuh.
 #include "ntt.cuh"
 
 namespace ppst {
 
-template <int S>
-__global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS)
+template <int S, int SUB>
+__global__ void __launch_bounds__(PassShape<S, SUB>::THREADS, PassShape<S, SUB>::MIN_BLOCKS)
     k_ntt_fwd_cols(LimbMap map, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN)
 {
-    typedef PassShape<S> P;
+    typedef PassShape<S, SUB> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN, C = N >> S;
     const int b = blockIdx.y, p = map.prime(b);
     uint64_t *a = map.ptr(b, N);
     const uint64_t q = pc[p].q;
     int h, sub;
-    pass_coords<S, true>(h, sub);
+    pass_coords<S, true, SUB>(h, sub);
     const int g = blockIdx.x * P::SUB + sub;
     uint64_t x[P::E];
 #pragma unroll
     for (int k = 0; k < P::E; k++) x[k] = a[(size_t)(h + P::T * k) * C + g];
-    cols_fwd_core<S>(x, sm, h, sub, tw + (size_t)p * N, q);
+    cols_fwd_core<S, SUB>(x, sm, h, sub, tw + (size_t)p * N, q);
 #pragma unroll
     for (int k = 0; k < P::E; k++) a[(size_t)(P::E * h + k) * C + g] = x[k];
 }
 
-template <int S>
-__global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS)
+template <int S, int SUB>
+__global__ void __launch_bounds__(PassShape<S, SUB>::THREADS, PassShape<S, SUB>::MIN_BLOCKS)
     k_ntt_fwd_chunks(LimbMap map, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN)
 {
-    typedef PassShape<S> P;
+    typedef PassShape<S, SUB> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN;
     const int b = blockIdx.y, p = map.prime(b);
     const uint64_t q = pc[p].q;
     int h, sub;
-    pass_coords<S, false>(h, sub);
+    pass_coords<S, false, SUB>(h, sub);
     const int g = blockIdx.x * P::SUB + sub;
     uint64_t *a = map.ptr(b, N) + (size_t)g * P::M;
     uint64_t x[P::E];
@@ -61,17 +62,17 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCK
     for (int k = 0; k < P::E; k++) a[h + P::T * k] = reduce4q(x[k], q);
 }
 
-template <int S>
-__global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS)
+template <int S, int SUB>
+__global__ void __launch_bounds__(PassShape<S, SUB>::THREADS, PassShape<S, SUB>::MIN_BLOCKS)
     k_ntt_inv_chunks(LimbMap map, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN)
 {
-    typedef PassShape<S> P;
+    typedef PassShape<S, SUB> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN;
     const int b = blockIdx.y, p = map.prime(b);
     const uint64_t q = pc[p].q;
     int h, sub;
-    pass_coords<S, false>(h, sub);
+    pass_coords<S, false, SUB>(h, sub);
     const int g = blockIdx.x * P::SUB + sub;
     uint64_t *a = map.ptr(b, N) + (size_t)g * P::M;
     uint64_t x[P::E];
@@ -84,33 +85,42 @@ __global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCK
 
 // last inverse pass; the result is multiplied by N^-1, or by outmul[i] for limb
 // i of its polynomial (N^-1 times a constant of the caller's), and reduced to [0, q)
-template <int S>
-__global__ void __launch_bounds__(PassShape<S>::THREADS, PassShape<S>::MIN_BLOCKS)
+template <int S, int SUB>
+__global__ void __launch_bounds__(PassShape<S, SUB>::THREADS, PassShape<S, SUB>::MIN_BLOCKS)
     k_ntt_inv_cols(LimbMap map, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN,
                    const Tw *__restrict__ outmul)
 {
-    typedef PassShape<S> P;
+    typedef PassShape<S, SUB> P;
     __shared__ uint64_t sm[P::SMEM_WORDS];
     const int N = 1 << logN, C = N >> S;
     const int b = blockIdx.y, p = map.prime(b);
     uint64_t *a = map.ptr(b, N);
     const uint64_t q = pc[p].q;
     int h, sub;
-    pass_coords<S, true>(h, sub);
+    pass_coords<S, true, SUB>(h, sub);
     const int g = blockIdx.x * P::SUB + sub;
     uint64_t x[P::E];
 #pragma unroll
     for (int k = 0; k < P::E; k++) x[k] = a[(size_t)(P::E * h + k) * C + g];
-    cols_inv_core<S>(x, sm, h, sub, tw + (size_t)p * N, q);
+    cols_inv_core<S, SUB>(x, sm, h, sub, tw + (size_t)p * N, q);
     const Tw f = outmul ? outmul[b % map.per_poly] : Tw{pc[p].ninv, pc[p].ninv_sh};
 #pragma unroll
     for (int k = 0; k < P::E; k++) a[(size_t)(h + P::T * k) * C + g] = csub(shoup(x[k], f.w, f.s, q), q);
 }
 
-template <int S>
+template <int S, int SUB>
 static dim3 pass_grid(const Ctx &c, const LimbMap &m)
 {
-    return dim3((c.N >> S) / PassShape<S>::SUB, m.count());
+    return dim3((c.N >> S) / SUB, m.count());
+}
+
+// runs f(S, SUB) with the pass size of `s` and the block shape pass_sub picks for m
+template <class F>
+static void dispatch_pass(const Ctx &c, int s, const LimbMap &m, F &&f)
+{
+    dispatch_s(s, [&](auto sv) {
+        dispatch_sub<decltype(sv)::value>(pass_sub(c, decltype(sv)::value, m.count()), [&](auto bv) { f(sv, bv); });
+    });
 }
 
 void ntt_fwd(Ctx &c, const LimbMap &m)
@@ -118,17 +128,18 @@ void ntt_fwd(Ctx &c, const LimbMap &m)
     if (m.count() == 0) return;
     {
         ProfScope _ps(c, "ntt_cols_fwd", (uint64_t)2 * m.count());
-        dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
-            constexpr int S = decltype(sv)::value;
-            launch_on(c, k_ntt_fwd_cols<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twf,
-                c.logN);
+        dispatch_pass(c, ntt_s_rows(c.logN), m, [&](auto sv, auto bv) {
+            constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
+            launch_on(c, k_ntt_fwd_cols<S, SUB>, pass_grid<S, SUB>(c, m), PassShape<S, SUB>::THREADS, 0, m, c.d_pc,
+                c.d_twf, c.logN);
         });
         check_launch("ntt_cols_fwd");
     }
     ProfScope _ps(c, "ntt_chunks_fwd", (uint64_t)2 * m.count());
-    dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
-        constexpr int S = decltype(sv)::value;
-        launch_on(c, k_ntt_fwd_chunks<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twf, c.logN);
+    dispatch_pass(c, ntt_s_chunk(c.logN), m, [&](auto sv, auto bv) {
+        constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
+        launch_on(c, k_ntt_fwd_chunks<S, SUB>, pass_grid<S, SUB>(c, m), PassShape<S, SUB>::THREADS, 0, m, c.d_pc,
+            c.d_twf, c.logN);
     });
     check_launch("ntt_chunks_fwd");
 }
@@ -138,10 +149,10 @@ void ntt_inv_mul(Ctx &c, const LimbMap &m, const Tw *outmul)
     if (m.count() == 0) return;
     {
         ProfScope _ps(c, "ntt_chunks_inv", (uint64_t)2 * m.count());
-        dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
-            constexpr int S = decltype(sv)::value;
-            launch_on(c, k_ntt_inv_chunks<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twi,
-                                                                                             c.logN);
+        dispatch_pass(c, ntt_s_chunk(c.logN), m, [&](auto sv, auto bv) {
+            constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
+            launch_on(c, k_ntt_inv_chunks<S, SUB>, pass_grid<S, SUB>(c, m), PassShape<S, SUB>::THREADS, 0, m,
+                c.d_pc, c.d_twi, c.logN);
         });
         check_launch("ntt_chunks_inv");
     }
@@ -152,10 +163,10 @@ void ntt_inv_cols_mul(Ctx &c, const LimbMap &m, const Tw *outmul)
 {
     if (m.count() == 0) return;
     ProfScope _ps(c, "ntt_cols_inv", (uint64_t)2 * m.count());
-    dispatch_s(ntt_s_rows(c.logN), [&](auto sv) {
-        constexpr int S = decltype(sv)::value;
-        launch_on(c, k_ntt_inv_cols<S>, pass_grid<S>(c, m), PassShape<S>::THREADS, 0, m, c.d_pc, c.d_twi, c.logN,
-                                                                                       outmul);
+    dispatch_pass(c, ntt_s_rows(c.logN), m, [&](auto sv, auto bv) {
+        constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
+        launch_on(c, k_ntt_inv_cols<S, SUB>, pass_grid<S, SUB>(c, m), PassShape<S, SUB>::THREADS, 0, m, c.d_pc,
+            c.d_twi, c.logN, outmul);
     });
     check_launch("ntt_cols_inv");
 }

@@ -35,11 +35,21 @@ struct PassShape {
     static constexpr int A = (S + 1) / 2;  // register stages before the transpose
     static constexpr int E = 1 << A;       // words per thread
     static constexpr int T = M / E;        // threads per sub-transform
-    static constexpr int SUB = SUB_;       // sub-transforms per block
+    static constexpr int SUB = SUB_;       // sub-transforms per block (4, 8 or 16)
     static constexpr int THREADS = SUB * T;
     static constexpr int SMEM_WORDS = SUB * (M + M / E);  // padded transpose buffer
-    static constexpr int MIN_BLOCKS = THREADS >= 256 ? 3 : 4;
+    static constexpr int MIN_BLOCKS = THREADS >= 256 ? 3 : (THREADS >= 128 ? 4 : 8);
 };
+
+// COLS passes keep row p of column `sub` at (p + p / E) SUB + sub: the pad
+// word every E rows keeps both transposes free of bank conflicts for any SUB
+// (a half-warp touches 16 / SUB rows that are either consecutive or E apart)
+template <int S, int SUB>
+__device__ __forceinline__ int cols_smem(int p)
+{
+    typedef PassShape<S, SUB> P;
+    return (p + p / P::E) * SUB;
+}
 
 // forward lazy butterfly: X, Y in [0, 4q) -> [0, 4q)
 __device__ __forceinline__ void bfly_fwd(uint64_t &X, uint64_t &Y, const Tw &w, uint64_t q, uint64_t q2)
@@ -126,10 +136,10 @@ __device__ __forceinline__ void cols_fwd_core(uint64_t (&x)[PassShape<S>::E], ui
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < P::E; k++) sm[(h + P::T * k) * P::SUB + sub] = x[k];
+    for (int k = 0; k < P::E; k++) sm[cols_smem<S, SUB>(h + P::T * k) + sub] = x[k];
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < P::E; k++) x[k] = sm[(P::E * h + k) * P::SUB + sub];
+    for (int k = 0; k < P::E; k++) x[k] = sm[cols_smem<S, SUB>(P::E * h + k) + sub];
 #pragma unroll
     for (int d = P::T / 2; d >= 1; d >>= 1) {
         const int mg = P::M / (2 * d);
@@ -239,10 +249,10 @@ __device__ __forceinline__ void cols_inv_core(uint64_t (&x)[PassShape<S>::E], ui
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < P::E; k++) sm[(P::E * h + k) * P::SUB + sub] = x[k];
+    for (int k = 0; k < P::E; k++) sm[cols_smem<S, SUB>(P::E * h + k) + sub] = x[k];
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < P::E; k++) x[k] = sm[(h + P::T * k) * P::SUB + sub];
+    for (int k = 0; k < P::E; k++) x[k] = sm[cols_smem<S, SUB>(h + P::T * k) + sub];
 #pragma unroll
     for (int s = 0; s < P::A; s++) {
         const int d = P::T << s;
@@ -253,6 +263,17 @@ __device__ __forceinline__ void cols_inv_core(uint64_t (&x)[PassShape<S>::E], ui
             bfly_inv(x[k], x[k + (1 << s)], ldtw(T + mg + (k >> (s + 1))), q, q2);
         }
     }
+}
+
+// calls f(std::integral_constant<int, sub>) for the sub-transforms per block of
+// a pass of size 2^S: 16, 8 or 4 at S = 8 (N = 2^15, 2^16), 16 or 4 below
+// (where 8 is rounded down to 4: fewer kernels to compile)
+template <int S, class F>
+void dispatch_sub(int sub, F &&f)
+{
+    if (sub == 16) f(std::integral_constant<int, 16>{});
+    else if (S == 8 && sub == 8) f(std::integral_constant<int, S == 8 ? 8 : 4>{});
+    else f(std::integral_constant<int, 4>{});
 }
 
 // calls f(std::integral_constant<int, s>) for the pass sizes of N = 2^10 .. 2^16
@@ -270,5 +291,16 @@ void dispatch_s(int s, F &&f)
 
 inline int ntt_s_rows(int logN) { return (logN + 1) / 2; }  // COLS pass: log2 R
 inline int ntt_s_chunk(int logN) { return logN / 2; }      // CHUNKS pass: log2 C
+
+// sub-transforms per block of a pass over `rows` limbs: the largest of 16, 8, 4
+// whose grid still has at least the context's minimum number of blocks (small
+// grids, at low levels, spread over more SMs with smaller blocks)
+inline int pass_sub(const Ctx &c, int S, int rows)
+{
+    const long per16 = (long)(c.N >> S) / 16 * rows;
+    if (per16 >= (long)c.pass_min_blocks) return 16;
+    if (2 * per16 >= (long)c.pass_min_blocks) return 8;
+    return 4;
+}
 
 }  // namespace ppst

@@ -257,3 +257,26 @@ def test_inner_product_tiles_agree(env, tile):
     with pytest.raises(pp.PpstError) as e:
         ctx.set_tile(5)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("min_blocks", [0, 1 << 20])
+def test_pass_block_shapes_agree(env, min_blocks):
+    """Every transform pass with 16 sub-transforms per block (0) or 4 (2^20), and
+    the inner product's smallest tile: HMult at two levels, a rotation and a
+    rotate-and-sum bit-exact against the oracle."""
+    import paper_2508_12093_gb300 as pp
+    ctx, sk, evk, oc, ok = env
+    _, oa, ga = fresh(env, 24)
+    _, ob, gb = fresh(env, 25)
+    ctx.set_pass_blocks(min_blocks)
+    try:
+        same(ctx, ctx.hmult(evk, ga, gb), oc.hmult(oa, ob, ok))
+        same(ctx, ctx.hmult(evk, ctx.drop(ga, 2), gb), oc.hmult(oc.drop(oa, 2), ob, ok))
+        same(ctx, ctx.rotate(evk, ga, 4), oc.rotate(oa, 4, ok))
+        same(ctx, ctx.rotsum(evk, ga), oc.rotsum(oa, ok))
+        same(ctx, ctx.mul_const(ga, 0.37), oc.mul_const(oa, 0.37))
+    finally:
+        ctx.set_pass_blocks(456)
+    with pytest.raises(pp.PpstError) as e:
+        ctx.set_pass_blocks((1 << 20) + 1)
+    assert e.value.code == -1

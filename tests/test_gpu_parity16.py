@@ -52,6 +52,16 @@ def test_every_dnum_full_size(dnum):
         ctx.set_tile(tile)
         check(ctx, ctx.hmult(evk, a, b), want[("hmult", 23)], f"dnum {dnum} hmult tile {tile}")
     ctx.set_tile(8)
+    # the block shapes the default picks elsewhere: 4 sub-transforms per block at
+    # the top level, 16 at level 1
+    ctx.set_pass_blocks(1 << 20)
+    check(ctx, ctx.hmult(evk, a, b), want[("hmult", 23)], f"dnum {dnum} hmult, 4 per block")
+    check(ctx, ctx.rotate(evk, a, oj.ROT), want[("rot", 23)], f"dnum {dnum} rotation, 4 per block")
+    ctx.set_pass_blocks(0)
+    a1 = ctx.drop(a, 1)
+    check(ctx, ctx.hmult(evk, a1, b), want[("hmult", 1)], f"dnum {dnum} hmult level 1, 16 per block")
+    check(ctx, ctx.rotate(evk, a1, oj.ROT), want[("rot", 1)], f"dnum {dnum} rotation level 1, 16 per block")
+    ctx.set_pass_blocks(456)
 
 
 @pytest.mark.oracle16("batch")
