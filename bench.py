@@ -40,12 +40,12 @@ WORKLOAD = ("N=2^16 (32768 slots), 24 Q primes (60+23x50 bit) + 4 special 60-bit
 # (2 x 2 x 24 limbs), the relinearisation key (6 x 2 x 28 limbs) and the output
 # (2 x 24 limbs) of 2^16 words each
 HMULT_BYTES = (2 * 2 * 24 + 6 * 2 * 28 + 2 * 24) * 65536 * 8
-# DRAM bytes per algorithmic byte of a kernel, from ncu captures: k_inner_chunks
-# in a single-item top-level HMult (python -m paper_2508_12093_gb300.profcase hmult)
-# read 294.1 MB and wrote 20.6 MB against 293.6 MB algorithmic (1.072); with three
-# items (profcase batch3) 540.9 MB against 528.5 MB (1.023). The single-item
-# ratio is used: the larger of the two
-DRAM_PER_ALG = {"inner_chunks": (294.05 + 20.55) / 293.6}
+# DRAM bytes per fused-kernel byte (the limbs a kernel reads once plus those it
+# writes, intermediates included) from ncu captures of the current kernels; the
+# per-launch traffic reported is this ratio times the launch's fused bytes.
+# Filled in from the capture of the kernel as it now stands (empty: none yet).
+DRAM_PER_FUSED = {}
+DRAM_SOURCE = None
 
 
 def peaks():
@@ -160,7 +160,8 @@ def step_op_work():
 
 class OracleSampler:
     """Times the oracle's top-level HMult, rotation and Mul(P) at N = 2^16 and
-    converts them to queries/s with the step's limb-weighted op trace."""
+    converts them to queries/s with the step's limb-weighted op trace (an
+    extrapolation: the ops are timed, the query is not)."""
 
     def __init__(self):
         from oracle import ckks as ock
@@ -171,6 +172,7 @@ class OracleSampler:
         self.work = step_op_work()
 
     def sample(self):
+        """(extrapolated queries/s, seconds this sample took, per-op seconds)."""
         t = {}
         t0 = time.perf_counter()
         self.c.hmult(self.ct, self.ct, self.keys)
@@ -187,8 +189,9 @@ class OracleSampler:
         step_s = sum(self.work[k] * t[k] for k in t)
         return len(STATS) / step_s, sum(t.values()), t
 
-    DESC = ("exact CPU oracle (Python + C, one thread): one top-level HMult+KeySwitch, rotation, Mul(P)+rescale "
-            "and Add at N=2^16 timed, scaled by the limb-weighted op counts of one step's schedule")
+    DESC = ("exact CPU oracle (Python + C): one top-level HMult+KeySwitch, rotation, Mul(P)+rescale and Add at "
+            "N=2^16 timed per process; queries/s EXTRAPOLATED from those op times with the limb-weighted op counts "
+            "of one step's schedule (a whole N=2^16 query takes minutes on the oracle)")
 
 
 def _oracle_worker(rounds):
@@ -197,33 +200,79 @@ def _oracle_worker(rounds):
     return [s.sample() for _ in range(rounds)]
 
 
-def oracle_on_cores(rounds, skip=0):
-    """The oracle on every host core (up to 16): one spawned process per core, each
-    computing its own independent queries; returns the aggregate queries/s of the
-    rounds after `skip` (the sum of the cores' rates), the cores used and the CPU
-    seconds of one core's round."""
+def oracle_on_cores(rounds, skip=0, cores=None):
+    """The oracle on `cores` host cores (default: all, up to 16): one spawned
+    process per core, each timing its own samples. Returns the aggregate
+    extrapolated queries/s of the rounds after `skip` (the sum of the cores'
+    rates), the cores used, the mean wall seconds of one round (the slowest
+    core's sample) and one core's per-op seconds."""
     import multiprocessing
-    cores = max(1, min(16, os.cpu_count() or 1))
+    cores = cores or max(1, min(16, os.cpu_count() or 1))
     with multiprocessing.get_context("spawn").Pool(cores) as pool:
         res = pool.map(_oracle_worker, [rounds] * cores)
     rates = [sum(r[k][0] for k in range(skip, rounds)) / (rounds - skip) for r in res]
-    secs = [r[k][1] for r in res for k in range(skip, rounds)]
-    return sum(rates), cores, sum(secs) / len(secs), res[0][-1][2]
+    round_s = [max(r[k][1] for r in res) for k in range(skip, rounds)]
+    return sum(rates), cores, sum(round_s) / len(round_s), res[0][-1][2]
+
+
+def _cfg1_query_worker(_):
+    """One real toy-set query on the oracle (N = 2^12, 12 Q primes): Z-score of
+    2048 uniform values, B = 0.29, degree 7, 2 Newton steps; its wall time."""
+    from oracle import ckks as ock
+    from oracle import stats as ost
+    prm = workloads.PARAMS["toy12"]
+    oc = ock.Ckks(ock.Params(**prm))
+    ok = oc.keygen(2, rotations=[1 << i for i in range(prm["log_n"] - 1)])
+    x = workloads.uniform_column(oc.prm.S, seed=1)
+    cts = oc.encrypt_column(ok["pk"], x, 3)
+    t0 = time.perf_counter()
+    ost.znorm(ost.CkksEv(oc, ok), cts, len(x), 0.29, 3, 2)
+    return time.perf_counter() - t0
+
+
+def cfg1_queries(cores):
+    """The toy-set Z-score query timed whole on the oracle: single thread, and
+    one independent query per core on `cores` cores."""
+    import multiprocessing
+    with multiprocessing.get_context("spawn").Pool(cores) as pool:
+        one = pool.map(_cfg1_query_worker, [0])[0]
+        many = pool.map(_cfg1_query_worker, range(cores))
+    return {"query": "N=2^12 toy set, Z-score of 2048 uniform values (B=0.29, degree 7, 2 Newton steps), timed whole",
+            "single_thread_s": one, "single_thread_queries_per_s": 1.0 / one,
+            "all_cores_queries_per_s": sum(1.0 / t for t in many), "cores": cores}
+
+
+def cpu_baseline_leg():
+    """The oracle as the reported CPU baseline: the bench workload's queries/s
+    extrapolated from timed N = 2^16 ops (single thread and all cores), and the
+    toy-set query timed whole."""
+    cores = max(1, min(16, os.cpu_count() or 1))
+    v1, _, s1, parts = oracle_on_cores(1, cores=1)
+    v, cores, dt, _ = oracle_on_cores(1, cores=cores)
+    return {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": (OracleSampler.DESC + f"; {cores} processes, one per host core, each on its own ops "
+                       f"({dt:.1f} s of CPU work per core)"),
+            "extrapolated": True, "single_thread_value": v1,
+            "op_seconds_single_thread": {k: round(t, 3) for k, t in parts.items()},
+            "timed_query_cfg1": cfg1_queries(cores)}
 
 
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    value, cores, dt, _ = oracle_on_cores(args.warmup + args.steps, skip=args.warmup)
-    ms_per_step = 1000.0 * len(STATS) / value
-    desc = OracleSampler.DESC + f"; {cores} processes, one per host core, each on its own queries"
+    value, cores, round_s, _ = oracle_on_cores(args.warmup + args.steps, skip=args.warmup)
+    desc = OracleSampler.DESC + f"; {cores} processes, one per host core, each on its own ops"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * round_s, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "queries_per_step": len(STATS)},
+            "config": {"workload": WORKLOAD, "queries_per_step": len(STATS),
+                       "step": ("one timed sample per core (HMult+KeySwitch, rotation, Mul(P), Add at N=2^16): "
+                                "ms_per_step is its wall time; value extrapolates those op times to queries/s"),
+                       "queries_equivalent_per_step": value * round_s},
             "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
-                             "sample": desc + f" ({dt:.1f} s of CPU work per core and step)"},
+                             "sample": desc + f" ({round_s:.1f} s of CPU work per core and step)",
+                             "extrapolated": True},
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -338,7 +387,7 @@ def main():
     launches = ctx.launch_count() - l0
     t_ms = e_start.elapsed_time(e_end)
     t_ms = replica_max(t_ms, dist)
-    n_dom, ms_dom, units_dom = ctx.prof_read(dom, with_units=True)
+    n_dom, ms_dom, units_dom, munits_dom = ctx.prof_read(dom, with_units=True, with_method=True)
     value = whole_job_rate(len(STATS) * args.steps, world, t_ms / 1000.0)
 
     # the plain form: the same queries one at a time
@@ -378,10 +427,13 @@ def main():
     peak, peak_kind = peaks()
     b64 = batched64(pp, ost, PARAMS, peak) if args.batched else None
 
-    # roofline of the dominant kernel: algorithmic bytes = the limbs it must
-    # read once plus the limbs it writes (the library counts them per launch)
+    # roofline of the dominant kernel: algorithmic bytes = the operation's own
+    # operands the kernel moves (the switching key for the inner product, once
+    # per batched launch; input / output ciphertexts elsewhere), not the
+    # intermediates the fused kernels exchange (the library counts both per launch)
     peak, peak_kind = peaks()
-    alg_bytes = units_dom * 8 * ctx.N
+    alg_bytes = munits_dom * 8 * ctx.N
+    fused_bytes = units_dom * 8 * ctx.N
     achieved = (alg_bytes / (ms_dom / 1000.0)) / 1e9 if ms_dom > 0 else None
 
     # HMult + key switch microbenchmark (top level, dnum = 6)
@@ -433,11 +485,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, dt, parts = oracle_on_cores(1)
-        cpu = {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle",
-               "sample": (OracleSampler.DESC + f"; {cores} processes, one per host core, each on its own queries "
-                          f"({dt:.1f} s of CPU work per core)"),
-               "op_seconds_per_core": {k: round(t, 3) for k, t in parts.items()}}
+        cpu = cpu_baseline_leg()
 
     if rank == 0:
         line = {
@@ -473,16 +521,16 @@ def main():
                          "frac_of_hbm": hmult_gbs / peak},
             "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if achieved else None,
-                         "traffic": (DRAM_PER_ALG[dom] * alg_bytes / max(1, n_dom)) if dom in DRAM_PER_ALG else None,
-                         "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per algorithmic byte of "
-                                            "a single-item top-level launch (1.072; 1.023 with three items), times "
-                                            "the algorithmic bytes per launch"
-                                            if dom in DRAM_PER_ALG else None),
+                         "traffic": (DRAM_PER_FUSED[dom] * fused_bytes / max(1, n_dom))
+                         if dom in DRAM_PER_FUSED else None,
+                         "traffic_source": (DRAM_SOURCE if dom in DRAM_PER_FUSED else None),
                          "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback",
                          "launches": n_dom, "avg_launch_us": 1000.0 * ms_dom / max(1, n_dom),
                          "share_of_step": shares[dom] / tot,
-                         "algorithmic_bytes_per_launch": alg_bytes / max(1, n_dom)},
+                         "algorithmic_bytes_per_launch": alg_bytes / max(1, n_dom),
+                         "algorithmic_bytes": "the switching key's limbs, once per batched launch (method operands)",
+                         "fused_kernel_bytes_per_launch": fused_bytes / max(1, n_dom)},
             "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

@@ -130,6 +130,13 @@ int ppst_ctx_set_tile(ppst_ctx *ctx, uint32_t inner_sub);
  * a grid of fewer than `min_blocks` blocks (default 456 = 3 x 152 SMs; 0: always
  * 16; 2^20: always 4). Changes speed only, never results. PPST_E_ARG above 2^20. */
 int ppst_ctx_set_pass_blocks(ppst_ctx *ctx, uint32_t min_blocks);
+/* Thread shape of the key-switching inner product (no counterpart in the
+ * paper): its transform pass keeps 16 (default) or 8 words per thread (8: one
+ * warp per 256-point chunk, three butterfly rounds; used at N = 2^15 and 2^16
+ * only, 16 elsewhere); lazy = 1 (8 words only) accumulates the key products
+ * exactly in 128 bits and reduces once per word. Speed only, never results.
+ * PPST_E_ARG for other values. */
+int ppst_ctx_set_inner_shape(ppst_ctx *ctx, uint32_t words_per_thread, uint32_t lazy);
 /* Failure-detection self-test (no counterpart in the paper): launches one block
  * that waits on a shared-memory barrier nothing completes, bounded by timeout_us
  * (1 .. 10^6); like the kernels with asynchronous copies, it records the timeout
@@ -318,13 +325,19 @@ int ppst_ticket_latency(ppst_server *srv, uint64_t ticket, double *seconds);
  * lincomb, elementwise, copy. ppst_prof_read synchronises, returns the launch
  * count, summed device time and summed algorithmic traffic of one class, and
  * forgets them; the traffic is counted in limbs of N words (8N bytes each), as
- * the limbs a kernel must read once plus the limbs it writes. ppst_prof_classes
+ * the limbs a kernel must read once plus the limbs it writes (`units`), and as
+ * the limbs of the operation's own operands it moves (`method_units`, may be
+ * NULL): the input and output ciphertexts and the switching key, each counted
+ * once per batched launch, not the intermediates the fused kernels exchange
+ * (HMult + key switch at the top level, dnum = 6: 4 x 24 input limbs for the
+ * tensor product, 6 x 2 x 28 key limbs for the inner product, 2 x 23 output
+ * limbs for the last ModDown pass). ppst_prof_classes
  * writes the recorded class names, comma separated. ppst_launch_count: kernels
  * this context has launched so far (always counted, profiling on or off). */
 int ppst_prof_start(ppst_ctx *ctx, const char *kernel_class);
 int ppst_prof_stop(ppst_ctx *ctx);
 int ppst_prof_read(ppst_ctx *ctx, const char *kernel_class, uint64_t *launches, double *total_ms,
-                   uint64_t *units);
+                   uint64_t *units, uint64_t *method_units);
 int ppst_prof_classes(ppst_ctx *ctx, char *buf, size_t cap);
 int ppst_launch_count(const ppst_ctx *ctx, uint64_t *launches);
 

@@ -444,6 +444,10 @@ class Context:
         self.inner_sub = int(inner_sub)
 
 
+    def set_inner_shape(self, words_per_thread, lazy=False):
+        """ppst_ctx_set_inner_shape: 16 or 8 words per thread in the inner product (speed only)."""
+        self._check(lib.ppst_ctx_set_inner_shape(self.ptr, int(words_per_thread), int(bool(lazy))))
+
     def set_pass_blocks(self, min_blocks):
         """ppst_ctx_set_pass_blocks: smaller transform blocks below this grid size (speed only)."""
         self._check(lib.ppst_ctx_set_pass_blocks(self.ptr, int(min_blocks)))
@@ -467,11 +471,13 @@ class Context:
         self._check(lib.ppst_prof_classes(self.ptr, buf, 4096))
         return [s for s in buf.value.decode().split(",") if s]
 
-    def prof_read(self, kernel_class, with_units=False):
-        n, ms, u = _lib.c_u64(), ctypes.c_double(), _lib.c_u64()
+    def prof_read(self, kernel_class, with_units=False, with_method=False):
+        """(launches, ms[, units][, method_units]) of a kernel class since prof_start."""
+        n, ms, u, mu = _lib.c_u64(), ctypes.c_double(), _lib.c_u64(), _lib.c_u64()
         self._check(lib.ppst_prof_read(self.ptr, kernel_class.encode(), ctypes.byref(n), ctypes.byref(ms),
-                                       ctypes.byref(u)))
-        return (n.value, ms.value, u.value) if with_units else (n.value, ms.value)
+                                       ctypes.byref(u), ctypes.byref(mu)))
+        out = (n.value, ms.value) + ((u.value,) if with_units else ()) + ((mu.value,) if with_method else ())
+        return out
 
     def launch_count(self):
         n = _lib.c_u64()

@@ -79,6 +79,7 @@ SIGNATURES = {
     "ppst_selftest_wait": (c_int, [c_void_p, c_u32]),
     "ppst_ctx_set_tile": (c_int, [c_void_p, c_u32]),
     "ppst_ctx_set_pass_blocks": (c_int, [c_void_p, c_u32]),
+    "ppst_ctx_set_inner_shape": (c_int, [c_void_p, c_u32, c_u32]),
     "ppst_inv_sqrt": (c_int, [c_void_p, c_void_p, c_void_p, c_double, ctypes.c_int32, ctypes.c_int32, PP]),
     "ppst_rescale": (c_int, [c_void_p, c_void_p, PP]),
     "ppst_add": (c_int, [c_void_p, c_void_p, c_void_p, PP]),
@@ -96,7 +97,7 @@ SIGNATURES = {
     "ppst_plan_run": (c_int, [c_void_p, PP]),
     "ppst_prof_start": (c_int, [c_void_p, ctypes.c_char_p]),
     "ppst_prof_stop": (c_int, [c_void_p]),
-    "ppst_prof_read": (c_int, [c_void_p, ctypes.c_char_p, P(c_u64), P(ctypes.c_double), P(c_u64)]),
+    "ppst_prof_read": (c_int, [c_void_p, ctypes.c_char_p, P(c_u64), P(ctypes.c_double), P(c_u64), P(c_u64)]),
     "ppst_launch_count": (c_int, [c_void_p, P(c_u64)]),
     "ppst_prof_classes": (c_int, [c_void_p, ctypes.c_char_p, c_size_t]),
     "ppst_free": (None, [c_void_p]),

@@ -103,6 +103,18 @@ int ppst_ctx_set_tile(ppst_ctx *ctx, uint32_t inner_sub)
     });
 }
 
+int ppst_ctx_set_inner_shape(ppst_ctx *ctx, uint32_t words_per_thread, uint32_t lazy)
+{
+    Ctx *c = (Ctx *)ctx;
+    if (!ok(c, TAG_CTX)) return PPST_E_ARG;
+    return guard(c, [&] {
+        REQ(words_per_thread == 8 || words_per_thread == 16, "words_per_thread must be 8 or 16");
+        REQ(lazy <= 1 && (lazy == 0 || words_per_thread == 8), "lazy accumulation needs 8 words per thread");
+        c->inner_words = (int)words_per_thread;
+        c->inner_lazy = lazy != 0;
+    });
+}
+
 int ppst_ctx_set_pass_blocks(ppst_ctx *ctx, uint32_t min_blocks)
 {
     Ctx *c = (Ctx *)ctx;
@@ -614,14 +626,15 @@ int ppst_prof_stop(ppst_ctx *ctx)
     return PPST_OK;
 }
 
-int ppst_prof_read(ppst_ctx *ctx, const char *kernel_class, uint64_t *launches, double *total_ms, uint64_t *units)
+int ppst_prof_read(ppst_ctx *ctx, const char *kernel_class, uint64_t *launches, double *total_ms, uint64_t *units,
+                   uint64_t *method_units)
 {
     Ctx *c = (Ctx *)ctx;
     if (!ok(c, TAG_CTX) || !kernel_class) return PPST_E_ARG;
     return guard(c, [&] {
         PPST_CUDA(cudaStreamSynchronize(c->stream));
         auto it = c->prof.rec.find(kernel_class);
-        uint64_t n = 0, u = 0;
+        uint64_t n = 0, u = 0, mu = 0;
         double ms = 0;
         if (it != c->prof.rec.end()) {
             for (auto &pr : it->second) {
@@ -630,6 +643,7 @@ int ppst_prof_read(ppst_ctx *ctx, const char *kernel_class, uint64_t *launches, 
                 ms += t;
                 n++;
                 u += pr.units;
+                mu += pr.munits;
                 c->prof.spare.push_back(pr.b);
                 c->prof.spare.push_back(pr.e);
             }
@@ -638,6 +652,7 @@ int ppst_prof_read(ppst_ctx *ctx, const char *kernel_class, uint64_t *launches, 
         if (launches) *launches = n;
         if (total_ms) *total_ms = ms;
         if (units) *units = u;
+        if (method_units) *method_units = mu;
     });
 }
 

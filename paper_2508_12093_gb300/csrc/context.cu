@@ -32,7 +32,7 @@ cudaEvent_t Prof::take()
     return e;
 }
 
-ProfScope::ProfScope(Ctx &cc, const char *k, uint64_t u) : c(cc), cls(k), units(u)
+ProfScope::ProfScope(Ctx &cc, const char *k, uint64_t u, uint64_t mu) : c(cc), cls(k), units(u), munits(mu)
 {
     c.prof.launches++;
     if (c.prof.on && (c.prof.only.empty() || c.prof.only == cls)) {
@@ -46,7 +46,7 @@ ProfScope::~ProfScope()
     if (!b) return;
     cudaEvent_t e = c.prof.take();
     cudaEventRecord(e, c.stream);
-    c.prof.rec[cls].push_back(ProfRec{b, e, units});
+    c.prof.rec[cls].push_back(ProfRec{b, e, units, munits});
 }
 
 // ---------------------------------------------------------------------------

@@ -112,7 +112,8 @@ struct MdC {
 // per-kernel-class timing with CUDA events on the launching stream
 struct ProfRec {
     cudaEvent_t b, e;
-    uint64_t units;  // work units of the launch (limbs for transforms and elementwise kernels)
+    uint64_t units;   // work units of the launch (limbs for transforms and elementwise kernels)
+    uint64_t munits;  // limbs of the op's own inputs and outputs (ciphertexts, keys) the launch moves
 };
 struct Prof {
     bool on = false;
@@ -177,6 +178,8 @@ struct Ctx {
     int ws_items = 0;
     size_t ws_bytes = 0;
     int inner_sub = 8;  // chunks per block of the key inner product (4, 8 or 16; autotuned)
+    int inner_words = 16;  // words per thread of the inner product's transform (16, or 8 at N >= 2^15)
+    bool inner_lazy = false;  // 8 words: accumulate the key products in 128 bits, reduce once
 
     size_t ct_words() const { return (size_t)2 * (L + 1) * N; }
     size_t ext_rows() const { return (size_t)(L + 1 + K); }
@@ -212,9 +215,9 @@ void check_launch(const char *what);
 struct ProfScope {
     Ctx &c;
     const char *cls;
-    uint64_t units;
+    uint64_t units, munits;
     cudaEvent_t b = nullptr;
-    ProfScope(Ctx &cc, const char *k, uint64_t u = 0);
+    ProfScope(Ctx &cc, const char *k, uint64_t u = 0, uint64_t mu = 0);
     ~ProfScope();
 };
 

@@ -266,6 +266,201 @@ __global__ void __launch_bounds__(InnerSmem<S, SUB>::THREADS, InnerSmem<S, SUB>:
 }
 
 // ---------------------------------------------------------------------------
+// 3'. the same stage with 8 words per thread (N = 2^15, 2^16: 256-point chunks)
+// ---------------------------------------------------------------------------
+// One warp per chunk (T = 32 threads x E = 8 words), three rounds of butterflies
+// (distances 128..32, 16..4, 2..1) with two warp-local exchanges through a
+// swizzled shared-memory buffer, so a thread holds half the registers of the
+// 16-word form and more warps fit on an SM. LAZY: the products with the key are
+// accumulated exactly in 128 bits over all digits and reduced once per word
+// (sum x k 2^64 < nd q^2 < 2^128 for nd <= 64 digits and q < 2^61).
+template <int SUB_>
+struct Inner8Smem {
+    static constexpr int M = 256, E = 8, T = 32;
+    static constexpr int SUB = SUB_;              // chunks per block (one warp each)
+    static constexpr int THREADS = SUB * T;
+    static constexpr int TILE = SUB * M;
+    static constexpr size_t X_OFF = 128;                              // two digit tiles
+    static constexpr size_t K_OFF = X_OFF + 2 * (size_t)TILE * 8;    // two key tiles
+    static constexpr size_t T_OFF = K_OFF + 2 * (size_t)TILE * 8;    // exchange buffers
+    static constexpr size_t BYTES = T_OFF + (size_t)TILE * 8;
+};
+
+// XOR swizzle of a chunk's 256 words: the three layouts a warp uses (h + 32 k,
+// 32 (h >> 2) + 4 k + (h & 3), 8 h + k) each touch 16 distinct 8-byte banks
+// per half-warp
+__device__ __forceinline__ int swz8(int p) { return p ^ ((p >> 4) & 7) ^ (((p >> 5) & 1) << 3); }
+
+// where natural word p of a 256-word chunk is stored in the evaluation domain
+// (the 16-word storage order of ntt.cuh: E h + k -> h + 16 k)
+__device__ __forceinline__ int addr16(int p) { return (p >> 4) + ((p & 15) << 4); }
+
+// forward CHUNKS pass of chunk g, 8 words per thread: words h + 32 k in, 8 h + k out
+__device__ __forceinline__ void chunks_fwd_core8(uint64_t (&x)[8], uint64_t *ex, int h, int g, int N,
+                                                 const Tw *__restrict__ T, uint64_t q)
+{
+    const uint64_t q2 = 2 * q;
+#pragma unroll
+    for (int s = 2; s >= 0; s--) {  // d = 32 << s: group (h + 32 k) / 2d = k >> (s + 1)
+        const int d = 32 << s;
+        const int base = N / (2 * d) + g * (256 / (2 * d));
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if ((k >> s) & 1) continue;
+            bfly_fwd(x[k], x[k + (1 << s)], ldtw(T + base + (k >> (s + 1))), q, q2);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 8; k++) ex[swz8(h + 32 * k)] = x[k];
+    __syncwarp();
+    const int hh = h >> 2, hl = h & 3;
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = ex[swz8(32 * hh + 4 * k + hl)];
+#pragma unroll
+    for (int s = 2; s >= 0; s--) {  // d = 4 << s: group p / 2d = (hh << (2 - s)) | (k >> (s + 1))
+        const int d = 4 << s;
+        const int base = N / (2 * d) + g * (256 / (2 * d)) + (hh << (2 - s));
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if ((k >> s) & 1) continue;
+            bfly_fwd(x[k], x[k + (1 << s)], ldtw(T + base + (k >> (s + 1))), q, q2);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 8; k++) ex[swz8(32 * hh + 4 * k + hl)] = x[k];
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = ex[swz8(8 * h + k)];
+#pragma unroll
+    for (int s = 1; s >= 0; s--) {  // d = 1 << s: group (8 h + k) / 2d
+        const int d = 1 << s;
+        const int base = N / (2 * d) + g * (256 / (2 * d));
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if ((k >> s) & 1) continue;
+            bfly_fwd(x[k], x[k + d], ldtw(T + base + ((8 * h + k) >> (s + 1))), q, q2);
+        }
+    }
+}
+
+template <int SUB, bool LAZY>
+__global__ void __launch_bounds__(Inner8Smem<SUB>::THREADS, SUB == 8 ? 2 : 4)
+    k_inner8(const uint64_t *__restrict__ ext, const uint64_t *__restrict__ d2n, const uint64_t *__restrict__ key,
+             uint64_t *__restrict__ acc, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN, int level,
+             int alpha, int L, int K, int nd, size_t ext_stride, int B, Ws ws, int *err)
+{
+    typedef Inner8Smem<SUB> SM;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);  // [0], [1]: digit stages; [2]: key stage
+    uint64_t *xs = reinterpret_cast<uint64_t *>(smem + SM::X_OFF);
+    uint64_t *ks = reinterpret_cast<uint64_t *>(smem + SM::K_OFF);
+    constexpr uint32_t TB = SM::TILE * 8;
+    const int N = 1 << logN;
+    const int it = blockIdx.x % B, tile = blockIdx.x / B;
+    const int e = blockIdx.y;
+    const int row = e <= level ? e : L + 1 + (e - level - 1);
+    const PrimeC p = pc[row];
+    const Tw *T = tw + (size_t)row * N;
+    const size_t krow = (size_t)(L + 1 + K) * N;
+    const size_t t0 = (size_t)tile * SM::TILE;
+    const uint64_t *exte = ext + it * ws.ext + (size_t)e * N + t0;
+    const uint64_t *d2ne = d2n + it * ws.d2 + (size_t)e * N + t0;
+    const uint64_t *keye = key + (size_t)row * N + t0;
+    auto own = [&](int j) { return e >= j * alpha && e < min(j * alpha + alpha, level + 1); };
+    auto load_digit = [&](int j) {
+        mbar_arrive_expect_tx(&bar[j & 1], TB);
+        bulk_g2s(xs + (j & 1) * SM::TILE, own(j) ? d2ne : exte + (size_t)j * ext_stride, TB, &bar[j & 1]);
+    };
+    auto load_keys = [&](int j) {
+        mbar_arrive_expect_tx(&bar[2], 2 * TB);
+        bulk_g2s(ks, keye + (size_t)j * 2 * krow, TB, &bar[2]);
+        bulk_g2s(ks + SM::TILE, keye + (size_t)j * 2 * krow + krow, TB, &bar[2]);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init(&bar[2], 1);
+        mbar_fence_init();
+        fence_proxy_async_smem();
+        load_digit(0);
+        if (nd > 1) load_digit(1);
+        load_keys(0);
+    }
+    __syncthreads();
+    const int h = threadIdx.x & 31, sub = threadIdx.x >> 5;
+    const int g = tile * SUB + sub;
+    uint64_t *ex = reinterpret_cast<uint64_t *>(smem + SM::T_OFF) + sub * SM::M;
+    int ka[8];  // tile offsets (storage order) of this thread's output words 8 h + k
+#pragma unroll
+    for (int k = 0; k < 8; k++) ka[k] = sub * SM::M + addr16(8 * h + k);
+    uint64_t a0[8], a1[8], b0[8], b1[8];  // LAZY: (lo, hi) = (a, b); else a only
+#pragma unroll
+    for (int k = 0; k < 8; k++) a0[k] = a1[k] = b0[k] = b1[k] = 0;
+    int j = 0;
+    for (; j < nd; j++) {
+        if (__syncthreads_or(!mbar_wait(&bar[j & 1], (j >> 1) & 1))) break;
+        uint64_t x[8];
+        const uint64_t *xt = xs + (j & 1) * SM::TILE;
+        if (own(j)) {  // already in the evaluation domain, storage order (block-uniform)
+#pragma unroll
+            for (int k = 0; k < 8; k++) x[k] = xt[ka[k]];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; k++) x[k] = xt[sub * SM::M + h + 32 * k];
+            chunks_fwd_core8(x, ex, h, g, N, T, p.q);
+#pragma unroll
+            for (int k = 0; k < 8; k++) x[k] = reduce4q(x[k], p.q);
+        }
+        if (__syncthreads_or(!mbar_wait(&bar[2], j & 1))) break;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const uint64_t k0 = ks[ka[k]], k1 = ks[SM::TILE + ka[k]];
+            if (LAZY) {
+                Acc128 u{a0[k], b0[k]}, v{a1[k], b1[k]};
+                mac(u, x[k], k0);
+                mac(v, x[k], k1);
+                a0[k] = u.lo;
+                b0[k] = u.hi;
+                a1[k] = v.lo;
+                b1[k] = v.hi;
+            } else {
+                a0[k] = add_mod(a0[k], mont_mul(x[k], k0, p.q, p.qinv), p.q);
+                a1[k] = add_mod(a1[k], mont_mul(x[k], k1, p.q, p.qinv), p.q);
+            }
+        }
+        __syncthreads();  // digit stage j & 1 and the key stage are free again
+        if (threadIdx.x == 0) {
+            fence_proxy_async_smem();  // the CTA's reads of those stages before the copies that refill them
+            if (j + 2 < nd) load_digit(j + 2);
+            if (j + 1 < nd) load_keys(j + 1);
+        }
+    }
+    if (j < nd) {  // a copy did not arrive in time: report, drain what is in flight, give up
+        if (threadIdx.x == 0) {
+            *(volatile int *)err = 1;
+            for (int d = j; d < min(j + 2, nd); d++) mbar_wait(&bar[d & 1], (d >> 1) & 1);
+            mbar_wait(&bar[2], j & 1);
+        }
+        return;
+    }
+    uint64_t *o0 = acc + it * ws.acc + (size_t)e * N + t0, *o1 = o0 + krow;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        if (LAZY) {  // (hi mod q) 2^64 + lo, then one Montgomery reduction
+            const uint64_t h0 = csub(shoup(b0[k], 1, p.w64, p.q), p.q);
+            const uint64_t h1 = csub(shoup(b1[k], 1, p.w64, p.q), p.q);
+            o0[ka[k]] = mont_redc(h0, a0[k], p.q, p.qinv);
+            o1[ka[k]] = mont_redc(h1, a1[k], p.q, p.qinv);
+        } else {
+            o0[ka[k]] = a0[k];
+            o1[ka[k]] = a1[k];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // failure-detection self-test: one block waits on a barrier whose phase never
 // completes (nothing is copied), gives up after limit_ns, records the timeout in
 // the error word and returns, exactly as the pipelined kernels do
@@ -319,7 +514,9 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
     // per target limb: the two key words of every digit, read once for the
     // batch (its items run back to back on the same key tile); per item and
     // target limb: one digit word per digit read, two accumulators written
-    ProfScope _ps(c, "inner_chunks", (uint64_t)E_ext * 2 * nd + (uint64_t)B * E_ext * (nd + 2));
+    // method traffic: the switching key's limbs, once for the batch
+    ProfScope _ps(c, "inner_chunks", (uint64_t)E_ext * 2 * nd + (uint64_t)B * E_ext * (nd + 2),
+                  (uint64_t)E_ext * 2 * nd);
     auto launch = [&](auto sv, auto subv) {
         constexpr int S = decltype(sv)::value, SUB = decltype(subv)::value;
         typedef InnerSmem<S, SUB> SM;
@@ -333,11 +530,35 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
         launch_on(c, k_inner_chunks<S, SUB>, grid, SM::THREADS, SM::BYTES, c.ws_ext, c.ws_d2n, key.d, c.ws_acc,
             c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, B, ws, c.d_err);
     };
+    auto launch8 = [&](auto subv, auto lazyv) {
+        constexpr int SUB = decltype(subv)::value;
+        constexpr bool LAZY = decltype(lazyv)::value;
+        typedef Inner8Smem<SUB> SM;
+        const dim3 grid(B * (c.N / SM::TILE), E_ext);
+        static std::atomic<bool> attr_set{false};
+        if (!attr_set.load()) {
+            PPST_CUDA(cudaFuncSetAttribute(k_inner8<SUB, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)SM::BYTES));
+            attr_set = true;
+        }
+        launch_on(c, k_inner8<SUB, LAZY>, grid, SM::THREADS, SM::BYTES, c.ws_ext, c.ws_d2n, key.d, c.ws_acc,
+            c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, B, ws, c.d_err);
+    };
     dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
         // the context's tile, halved (down to 4 chunks) while the grid would leave SMs idle
         int tile = c.inner_sub;
         while (tile > 4 && (long)B * ((c.N >> S) / tile) * E_ext < (long)c.pass_min_blocks) tile /= 2;
+        if (S == 8 && c.inner_words == 8) {  // 8 words per thread: tiles of 4 or 8 chunks
+            if (tile >= 8) {
+                if (c.inner_lazy) launch8(std::integral_constant<int, 8>{}, std::true_type{});
+                else launch8(std::integral_constant<int, 8>{}, std::false_type{});
+            } else {
+                if (c.inner_lazy) launch8(std::integral_constant<int, 4>{}, std::true_type{});
+                else launch8(std::integral_constant<int, 4>{}, std::false_type{});
+            }
+            return;
+        }
         switch (tile) {
         case 4: launch(sv, std::integral_constant<int, 4>{}); break;
         case 16: launch(sv, std::integral_constant<int, 16>{}); break;
@@ -372,7 +593,7 @@ std::vector<CtObj *> ev_hmult_batch(Ctx &c, const EvkObj &k, const std::vector<c
             ip.out[i] = t[i]->d;
         }
         {
-            ProfScope _ps(c, "tensor", (uint64_t)B * 7 * (lv + 1));
+            ProfScope _ps(c, "tensor", (uint64_t)B * 7 * (lv + 1), (uint64_t)B * 4 * (lv + 1));  // reads a, b
             dispatch_pass(c, ntt_s_chunk(c.logN), B * (lv + 1), [&](auto sv, auto bv) {
                 constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
                 launch_on(c, k_tensor_ic<S, SUB>, grid_s(c, S, SUB, B * (lv + 1)), PassShape<S, SUB>::THREADS, 0,
@@ -429,7 +650,7 @@ std::vector<CtObj *> ev_rotate_batch(Ctx &c, const EvkObj &k, const std::vector<
             ip.out[i] = o[i]->d;
         }
         {
-            ProfScope _ps(c, "automorph", (uint64_t)B * 5 * (lv + 1));
+            ProfScope _ps(c, "automorph", (uint64_t)B * 5 * (lv + 1), (uint64_t)B * 2 * (lv + 1));  // reads a
             dispatch_pass(c, ntt_s_chunk(c.logN), B * (lv + 1), [&](auto sv, auto bv) {
                 constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
                 launch_on(c, k_automorph_ic<S, SUB>, grid_s(c, S, SUB, B * 2 * (lv + 1)),

@@ -334,7 +334,7 @@ void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip)
         });
         check_launch("k_md_cols");
     }
-    ProfScope _ps(c, "moddown_chunks", (uint64_t)B * (RESC ? 8 : 7) * nl);
+    ProfScope _ps(c, "moddown_chunks", (uint64_t)B * (RESC ? 8 : 7) * nl, (uint64_t)B * 2 * nl);  // writes out
     dispatch_pass(c, ntt_s_chunk(c.logN), B * 2 * nl, [&](auto sv, auto bv) {
         constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
         const size_t smem = MdSmem<S, SUB>::BYTES;

@@ -4,7 +4,7 @@
     python -m paper_2508_12093_gb300.profcase rotate     # N=2^16, 3 top-level rotations
     python -m paper_2508_12093_gb300.profcase query      # N=2^16, one kurtosis query
     python -m paper_2508_12093_gb300.profcase batch3     # N=2^16, skew/kurt/CV of three columns, one batch
-    python -m paper_2508_12093_gb300.profcase stages [dnum ...]  # per-kernel-class times (CUDA events)
+    python -m paper_2508_12093_gb300.profcase stages [dnum[:shape] ...]  # per-kernel-class times (CUDA events)
 
 Each case sets up keys and one ciphertext, runs a few warm-up iterations, then
 the profiled iterations, synchronises and prints "ok".
@@ -19,16 +19,24 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def stages(dnums=(6,), reps=20):
+SHAPES = {"e16": (16, False), "e8": (8, False), "e8lazy": (8, True)}
+
+
+def stages(specs=("6",), reps=20):
     """Per-kernel-class GPU time (CUDA events on the library's stream, mean of
     `reps` launches) of HMult and rotation at levels 23, 12 and 4, and the
-    whole op's median time, for each dnum; printed as one JSON line each."""
+    whole op's median time, for each spec "dnum" or "dnum:shape" (shape: e16,
+    e8, e8lazy: the inner product's words per thread); one JSON line each."""
     import json
     import torch
     import paper_2508_12093_gb300 as pp
     import workloads
-    for d in dnums:
+    for spec in specs:
+        d, _, shape = str(spec).partition(":")
+        d = int(d)
         ctx = pp.Context(workloads.PARAMS[f"n16_d{d}"])
+        if shape:
+            ctx.set_inner_shape(*SHAPES[shape])
         sk, evk = ctx.keygen(2, rotations=[1])
         a = ctx.encrypt_ints(evk, np.arange(ctx.N, dtype=np.int64) % 1000, 9, 0, 2.0 ** 50)
         for lv in (23, 12, 4):
@@ -55,14 +63,15 @@ def stages(dnums=(6,), reps=20):
                     n, ms = ctx.prof_read(k)
                     if n:
                         cls[k] = round(1000.0 * ms / reps, 2)
-                print(json.dumps({"dnum": d, "op": name, "level": lv, "median_us": round(ts[len(ts) // 2], 1),
+                print(json.dumps({"dnum": d, "shape": shape or "e16", "op": name, "level": lv,
+                                  "median_us": round(ts[len(ts) // 2], 1),
                                   "per_op_us_by_class": cls}), flush=True)
         ctx.close()
 
 
 def main(case):
     if case == "stages":
-        stages(tuple(int(v) for v in sys.argv[2:]) or (6,))
+        stages(tuple(sys.argv[2:]) or ("6",))
         return
     import paper_2508_12093_gb300 as pp
     import workloads

@@ -62,6 +62,17 @@ def test_every_dnum_full_size(dnum):
     check(ctx, ctx.hmult(evk, a1, b), want[("hmult", 1)], f"dnum {dnum} hmult level 1, 16 per block")
     check(ctx, ctx.rotate(evk, a1, oj.ROT), want[("rot", 1)], f"dnum {dnum} rotation level 1, 16 per block")
     ctx.set_pass_blocks(456)
+    # the inner product with 8 words per thread, plain and with 128-bit accumulation,
+    # in tiles of 8 and 4 chunks
+    for lazy in (False, True):
+        ctx.set_inner_shape(8, lazy)
+        for tile in (8, 4):
+            ctx.set_tile(tile)
+            what = f"dnum {dnum}, 8 words per thread, lazy {lazy}, tile {tile}"
+            check(ctx, ctx.hmult(evk, a, b), want[("hmult", 23)], what + ", hmult")
+            check(ctx, ctx.rotate(evk, ctx.drop(a, 8), oj.ROT), want[("rot", 8)], what + ", rotation level 8")
+    ctx.set_inner_shape(16, False)
+    ctx.set_tile(8)
 
 
 @pytest.mark.oracle16("batch")
