@@ -512,6 +512,9 @@ def main():
             "toy12_zscore": toy,
             "batched64": b64,
             "hmult_ks_by_dnum": ({str(r["dnum"]): {"us": r["hmult_us"], "tile": r["tile"], "us_by_tile": r["tile_us"],
+                                                   "inner": r.get("inner"), "us_by_inner_shape": r.get("inner_us"),
+                                                   "pass_min_blocks": r.get("pass_min_blocks"),
+                                                   "level4_us_by_pass_blocks": r.get("pass_blocks_us"),
                                                    "algorithmic_bytes": r["algorithmic_bytes"],
                                                    "frac_of_hbm": r.get("hmult_frac_of_hbm"),
                                                    "rotate_us": r["rotate_us"], "skew_query_ms": r["query_us"] / 1e3}
@@ -752,9 +755,10 @@ def batched64(pp, ost, params, peak):
     from paper_2508_12093_gb300 import autotune
     best, table = autotune.tune(params, cache=None, peak_gbs=peak)
     prm = autotune.with_dnum(params, best)
-    tile = next(r for r in table if r["dnum"] == best)["tile"]
+    row = next(r for r in table if r["dnum"] == best)
+    tile = row["tile"]
     ctx = pp.Context(prm)
-    ctx.set_tile(tile)
+    autotune.apply(ctx, row)
     sk, evk = ctx.keygen(2)
     cols, data = batched_columns(ctx, evk)
     qs = batched_queries(cols)
@@ -787,6 +791,7 @@ def batched64(pp, ost, params, peak):
     ctx.close()
     return {"value": len(qs) / batch_s, "unit": "queries/s", "serial_value": len(qs) / serial_s,
             "speedup_vs_serial": serial_s / batch_s, "queries": len(qs), "dnum": best, "inner_tile": tile,
+            "inner_shape": row.get("inner"), "pass_min_blocks": row.get("pass_min_blocks"),
             "gpu_launches": launches,
             "max_rel_err_vs_fp64": worst,
             "workload": (f"{BATCH_COLS} columns of log-uniform 1k-32k rows (one ciphertext each), in pairs of "

@@ -299,14 +299,33 @@ int ppst_plan_run(ppst_plan *plan, ppst_res **out);
 
 /* ---- serving (continuous batching) -----------------------------------------
  * A request loop on its own host threads (GPU work on the context's stream):
- * keys stay resident, queries
- * are admitted while their estimated working set fits `hbm_budget` bytes (and
- * at most `max_batch` run together), their ops are batched step by step, and
- * results are handed back by ticket. */
+ * keys stay resident, queries are admitted while their estimated working sets,
+ * plus the results finished but not yet handed over by ppst_wait, fit
+ * `hbm_budget` bytes (and at most `max_batch` run together); their ops are
+ * batched step by step, and results are handed back by ticket. Admission
+ * follows arrival order, except that a query which does not fit may be passed
+ * by later ones that do until it has waited 500 ms; from then on nothing
+ * passes it. hbm_budget = 0: the device memory free at creation (cudaMemGetInfo:
+ * keys and columns already resident are not free) plus the context pool's
+ * cached buffers, less 5 % of the device (PPST_E_BUDGET if nothing is left).
+ * The paper's server runs one query at a time (Sec. 4); the loop is this
+ * library's. */
+typedef struct {
+    size_t budget;    /* bytes the loop may use                             */
+    size_t reserved;  /* working-set estimates of the queries running       */
+    size_t held;      /* results finished and not yet taken by ppst_wait    */
+    uint32_t running; /* queries running                                    */
+    uint32_t queued;  /* queries waiting for admission                      */
+} ppst_server_stats;
 int ppst_server_create(ppst_ctx *ctx, const ppst_evk *evk, size_t hbm_budget, uint32_t max_batch,
                        ppst_server **out);
+int ppst_server_info(ppst_server *srv, ppst_server_stats *out);
+/* The admission estimate of a query (working set, result bytes), as submit
+ * computes it; PPST_E_ARG for an invalid query. */
+int ppst_server_estimate(ppst_server *srv, ppst_stat stat, const ppst_col *x, const ppst_col *y,
+                         size_t *working, size_t *result);
 /* Enqueue a query; returns immediately with a ticket. PPST_E_BUDGET if the
- * query alone can never fit the budget. */
+ * query alone (working set and result) can never fit the budget. */
 int ppst_submit(ppst_server *srv, ppst_stat stat, const ppst_col *x, const ppst_col *y,
                 const ppst_qopts *opts, uint64_t *ticket);
 /* Wait for a ticket (timeout_ms < 0: forever). PPST_E_TIMEOUT on timeout (the

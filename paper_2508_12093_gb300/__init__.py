@@ -160,6 +160,19 @@ class Server(_Handle):
         self.ctx._check(lib.ppst_ticket_latency(self.ptr, ticket, ctypes.byref(s)))
         return s.value
 
+    def info(self):
+        """ppst_server_info as a dict: budget, reserved, held, running, queued."""
+        o = _lib.ppst_server_stats()
+        self.ctx._check(lib.ppst_server_info(self.ptr, ctypes.byref(o)))
+        return {k: getattr(o, k) for k, _ in o._fields_}
+
+    def estimate(self, stat, x, y=None):
+        """(working-set bytes, result bytes) that admission reserves for a query."""
+        w, r = ctypes.c_size_t(), ctypes.c_size_t()
+        self.ctx._check(lib.ppst_server_estimate(self.ptr, STATS.get(stat, stat), x.ptr,
+                                                 y.ptr if y is not None else None, ctypes.byref(w), ctypes.byref(r)))
+        return w.value, r.value
+
 
 class Plan(_Handle):
     """A query captured as a CUDA graph (Context.prepare); run() replays it."""

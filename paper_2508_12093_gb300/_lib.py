@@ -45,6 +45,11 @@ class ppst_report(ctypes.Structure):
                 ("n_cts", c_u32)]
 
 
+class ppst_server_stats(ctypes.Structure):
+    _fields_ = [("budget", c_size_t), ("reserved", c_size_t), ("held", c_size_t), ("running", c_u32),
+                ("queued", c_u32)]
+
+
 u64p, i64p, f64p, i32p, u32p = P(c_u64), P(c_i64), P(ctypes.c_double), P(c_i32), P(c_u32)
 
 SIGNATURES = {
@@ -93,6 +98,8 @@ SIGNATURES = {
     "ppst_submit": (c_int, [c_void_p, c_int, c_void_p, c_void_p, P(ppst_qopts), P(c_u64)]),
     "ppst_wait": (c_int, [c_void_p, c_u64, c_i32, PP]),
     "ppst_ticket_latency": (c_int, [c_void_p, c_u64, P(c_double)]),
+    "ppst_server_info": (c_int, [c_void_p, P(ppst_server_stats)]),
+    "ppst_server_estimate": (c_int, [c_void_p, c_int, c_void_p, c_void_p, P(c_size_t), P(c_size_t)]),
     "ppst_query_prepare": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, P(ppst_qopts), PP]),
     "ppst_plan_run": (c_int, [c_void_p, PP]),
     "ppst_prof_start": (c_int, [c_void_p, ctypes.c_char_p]),

@@ -1,16 +1,21 @@
-"""Autotuner for the key-switching decomposition (dnum) and the inner-product
-tile of a parameter family.
+"""Autotuner for the key-switching decomposition (dnum), the inner product's
+thread shape and tile, and the transform passes' block shape of a parameter
+family.
 
 Hybrid key switching splits the Q chain into dnum digits of alpha = n_q / dnum
 primes and extends each digit over K = alpha special primes. Fewer digits
 mean fewer ModUp transforms and a smaller evaluation key but a wider base
 conversion and a longer ModDown; the key inner product's blocks own 4, 8 or 16
-transform chunks (more chunks: longer blocks, fewer per SM). Which choice is
-fastest is a property of the GPU, so it is measured: for every dnum the tuner
-builds a context with its own keys, times top-level HMult + key switch for each
-tile, then a rotation and one representative statistic query with the best
-tile, and picks the dnum with the fastest query. Results are cached in a JSON
-file keyed by device and parameters.
+transform chunks (more chunks: longer blocks, fewer per SM) with 16 or 8 words
+per thread (8: one warp per chunk, optionally with 128-bit lazy accumulation
+of the key products); the other transform passes switch to 8 or 4
+sub-transforms per block below a grid-size threshold. Which choice is fastest
+is a property of the GPU, so it is measured: for every dnum the tuner builds a
+context with its own keys, times top-level HMult + key switch for each inner
+shape, then low-level HMults for each block-shape threshold, then a rotation and
+one representative statistic query with the best shapes, and picks the dnum
+with the fastest query. Results are cached in a JSON file keyed by device and
+parameters. Every shape gives bit-identical results (tested).
 
     python -m paper_2508_12093_gb300.autotune [family] [--cache PATH]
 """
@@ -27,6 +32,9 @@ if ROOT not in sys.path:
 
 CANDIDATES = (3, 4, 6, 12)
 TILES = (4, 8, 16)  # transform chunks per block of the key inner product
+# inner-product shapes: (words per thread, 128-bit lazy accumulation, tile)
+INNER = ((16, False, 4), (16, False, 8), (16, False, 16), (8, False, 4), (8, False, 8), (8, True, 4), (8, True, 8))
+PASS_BLOCKS = (0, 228, 456, 912)  # grid-size thresholds for smaller transform blocks
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuned.json")
 
 
@@ -65,13 +73,28 @@ def measure(params, reps=20, query=None, peak_gbs=None):
     ctx = pp.Context(params)
     sk, evk = ctx.keygen(2)  # relinearisation key and the Galois keys of rotations by 2^i
     a = ctx.encrypt_ints(evk, np.zeros(ctx.N, dtype=np.int64), 9, 0, 2.0 ** params["log_scale"])
-    out = {"dnum": params["dnum"], "n_p": params["n_p"], "tile_us": {}}
-    for tile in TILES:
+    out = {"dnum": params["dnum"], "n_p": params["n_p"], "tile_us": {}, "inner_us": {}, "pass_blocks_us": {}}
+    for words, lazy, tile in INNER:
+        if words == 8 and params["log_n"] < 15:
+            continue  # 8 words per thread exist for 256-point chunks only
+        ctx.set_inner_shape(words, lazy)
         ctx.set_tile(tile)
-        out["tile_us"][str(tile)] = _timed(lambda: ctx.hmult(evk, a, a), reps)
-    out["tile"] = int(min(out["tile_us"], key=out["tile_us"].get))
-    ctx.set_tile(out["tile"])
-    out["hmult_us"] = out["tile_us"][str(out["tile"])]
+        t = _timed(lambda: ctx.hmult(evk, a, a), reps)
+        out["inner_us"][f"{words}{'L' if lazy else ''}/{tile}"] = t
+        if words == 16:
+            out["tile_us"][str(tile)] = t
+    best = min(out["inner_us"], key=out["inner_us"].get)
+    w, tile = best.split("/")
+    out["inner"] = {"words": int(w.rstrip("L")), "lazy": w.endswith("L"), "tile": int(tile)}
+    out["tile"] = int(tile)
+    apply(ctx, out)
+    out["hmult_us"] = out["inner_us"][best]
+    low = ctx.drop(a, min(4, params["n_q"] - 1))
+    for mb in PASS_BLOCKS:
+        ctx.set_pass_blocks(mb)
+        out["pass_blocks_us"][str(mb)] = _timed(lambda: ctx.hmult(evk, low, low), reps)
+    out["pass_min_blocks"] = int(min(out["pass_blocks_us"], key=out["pass_blocks_us"].get))
+    apply(ctx, out)
     out["rotate_us"] = _timed(lambda: ctx.rotate(evk, a, 1), reps)
     out["algorithmic_bytes"] = ks_bytes(params)
     out["hmult_gbs"] = out["algorithmic_bytes"] / (out["hmult_us"] * 1e-6) / 1e9
@@ -83,6 +106,15 @@ def measure(params, reps=20, query=None, peak_gbs=None):
     del a, sk, evk
     ctx.close()
     return out
+
+
+def apply(ctx, row):
+    """Set a measured row's shapes (inner product, transform blocks) on a context."""
+    inner = row.get("inner") or {"words": 16, "lazy": False, "tile": row.get("tile", 8)}
+    ctx.set_inner_shape(inner["words"], inner["lazy"])
+    ctx.set_tile(inner["tile"])
+    if "pass_min_blocks" in row:
+        ctx.set_pass_blocks(row["pass_min_blocks"])
 
 
 def _key(params):
@@ -127,11 +159,11 @@ def tuned_params(params, cache=DEFAULT_CACHE, **kw):
 
 
 def tuned_setup(params, cache=DEFAULT_CACHE, **kw):
-    """(params with the tuned dnum, the inner-product tile measured best for it);
-    apply the tile with Context.set_tile."""
+    """(params with the tuned dnum, its measured row); apply the row's shapes to
+    a context of those params with apply(ctx, row)."""
     best, table = tune(params, cache=cache, **kw)
     row = next(r for r in table if r["dnum"] == best)
-    return with_dnum(params, best), row["tile"]
+    return with_dnum(params, best), row
 
 
 if __name__ == "__main__":

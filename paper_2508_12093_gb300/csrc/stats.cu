@@ -890,7 +890,7 @@ struct Server {
     Sched sched;
     struct Ticket {
         QueryIn q;
-        size_t est = 0;
+        size_t est = 0, res_bytes = 0;  // working-set estimate; result ciphertexts held until ppst_wait
         std::chrono::steady_clock::time_point t_submit, t_ready;
         ResObj *res = nullptr;
         std::exception_ptr err;
@@ -901,8 +901,12 @@ struct Server {
     std::condition_variable cv_done, cv_compl, cv_idle;
     std::map<uint64_t, std::shared_ptr<Ticket>> tickets;
     std::deque<std::shared_ptr<Ticket>> queue, compl_q;
-    size_t reserved = 0;
+    size_t reserved = 0;  // working sets of the queries running
+    size_t held = 0;      // results finished but not yet handed over by ppst_wait
     uint32_t running = 0;
+    // a query that does not fit may be passed by later ones that do, until it has
+    // waited this long; from then on nothing passes it
+    std::chrono::milliseconds bypass_limit{500};
     uint64_t next_id = 1;
     bool stopping = false;
     std::thread sched_thread, compl_thread;
@@ -922,12 +926,26 @@ struct Server {
         return (n + 40) * ct_bytes + ws_item;
     }
 
-    // under mu
+    // bytes of a query's result ciphertexts (Z-score: one per input ciphertext)
+    size_t result_bytes(const QueryIn &q) const
+    {
+        return (q.stat == PPST_ZSCORE ? q.x->cts.size() : 1) * c->ct_words() * 8;
+    }
+
+    // under mu: admit, in arrival order, every queued query that fits the budget
+    // next to the running ones and the results not yet taken; a query that does
+    // not fit is passed only until it has waited bypass_limit
     void try_admit()
     {
-        while (!queue.empty() && running < max_batch && reserved + queue.front()->est <= budget) {
-            std::shared_ptr<Ticket> t = queue.front();
-            queue.pop_front();
+        const auto now = std::chrono::steady_clock::now();
+        for (auto it = queue.begin(); it != queue.end() && running < max_batch;) {
+            std::shared_ptr<Ticket> t = *it;
+            if (reserved + held + t->est + t->res_bytes > budget) {
+                if (now - t->t_submit >= bypass_limit) break;  // it is next; nothing passes it now
+                ++it;
+                continue;
+            }
+            it = queue.erase(it);
             reserved += t->est;
             running++;
             sched.worker_started();
@@ -956,6 +974,8 @@ struct Server {
         std::lock_guard<std::mutex> lk(mu);
         compl_q.push_back(t);
         reserved -= t->est;
+        if (!t->err) held += t->res_bytes;  // until ppst_wait hands the result over
+        else t->res_bytes = 0;
         running--;
         try_admit();
         cv_compl.notify_one();
@@ -995,7 +1015,8 @@ struct Server {
         auto t = std::make_shared<Ticket>();
         t->q = q;
         t->est = estimate(q);
-        if (t->est > budget) throw_err(PPST_E_BUDGET, "the query's working set exceeds the HBM budget");
+        t->res_bytes = result_bytes(q);
+        if (t->est + t->res_bytes > budget) throw_err(PPST_E_BUDGET, "the query's working set exceeds the HBM budget");
         std::lock_guard<std::mutex> lk(mu);
         if (stopping) throw_err(PPST_E_STATE, "server is shutting down");
         t->t_submit = std::chrono::steady_clock::now();
@@ -1017,10 +1038,23 @@ struct Server {
         if (timeout_ms < 0) cv_done.wait(lk, pred);
         else if (!cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred)) return PPST_E_TIMEOUT;
         t->taken = true;
+        held -= t->res_bytes;  // the caller owns the result now
+        t->res_bytes = 0;
+        try_admit();
         if (t->err) std::rethrow_exception(t->err);
         *out = t->res;
         t->res = nullptr;
         return PPST_OK;
+    }
+
+    void info(ppst_server_stats &o)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        o.budget = budget;
+        o.reserved = reserved;
+        o.held = held;
+        o.running = running;
+        o.queued = (uint32_t)queue.size();
     }
 
     double latency(uint64_t id)
@@ -1225,13 +1259,59 @@ int ppst_server_create(ppst_ctx *ctx, const ppst_evk *evk, size_t hbm_budget, ui
     const EvkObj *k = (const EvkObj *)evk;
     if (!out) return PPST_E_ARG;
     *out = nullptr;
-    if (!c || c->tag != TAG_CTX || !k || k->tag != TAG_EVK || k->ctx != c || max_batch < 1 || hbm_budget == 0)
-        return PPST_E_ARG;
+    if (!c || c->tag != TAG_CTX || !k || k->tag != TAG_EVK || k->ctx != c || max_batch < 1) return PPST_E_ARG;
     try {
+        if (hbm_budget == 0) {  // what the device has free now (keys and columns are resident already)
+            std::lock_guard<std::recursive_mutex> lk(c->exec_mu);
+            size_t free_b = 0, total_b = 0;
+            PPST_CUDA(cudaMemGetInfo(&free_b, &total_b));
+            size_t in_use = 0, cached = 0;
+            {
+                std::lock_guard<std::recursive_mutex> pl(c->pool.mu);
+                cached = c->pool.cached;
+                in_use = c->pool.in_use;
+            }
+            (void)in_use;
+            const size_t reserve = total_b / 20;  // 5 % of the device for everything else
+            hbm_budget = free_b + cached > reserve ? free_b + cached - reserve : 0;
+            if (hbm_budget == 0) return c->fail(PPST_E_BUDGET, "no device memory free for serving");
+        }
         *out = (ppst_server *)new Server(*c, *k, hbm_budget, max_batch);
         return PPST_OK;
+    } catch (const PpstError &e) {
+        return c->fail(e.code, e.msg);
     } catch (...) {
         return PPST_E_OOM;
+    }
+}
+
+int ppst_server_info(ppst_server *srv, ppst_server_stats *out)
+{
+    Server *s = (Server *)srv;
+    if (!s || s->tag != TAG_SRV || !out) return PPST_E_ARG;
+    s->info(*out);
+    return PPST_OK;
+}
+
+int ppst_server_estimate(ppst_server *srv, ppst_stat stat, const ppst_col *x, const ppst_col *y, size_t *working,
+                         size_t *result)
+{
+    Server *s = (Server *)srv;
+    if (!s || s->tag != TAG_SRV) return PPST_E_ARG;
+    try {
+        QueryIn q;
+        q.stat = stat;
+        q.x = (const ColObj *)x;
+        q.y = (const ColObj *)y;
+        q.o = ppst_qopts{1.0, 1.0, 7, 3};
+        validate_query(*s->c, q);
+        if (working) *working = s->estimate(q);
+        if (result) *result = s->result_bytes(q);
+        return PPST_OK;
+    } catch (const PpstError &e) {
+        return s->c->fail(e.code, e.msg);
+    } catch (...) {
+        return PPST_E_ARG;
     }
 }
 

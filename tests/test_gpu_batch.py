@@ -75,8 +75,9 @@ def test_autotune_picks_a_measured_dnum(tmp_path):
     again, _ = autotune.tune(base, cache=cache, candidates=(2, 3, 6), reps=3, query=q)  # from the cache
     assert again == best
     assert autotune.tuned_params(base, cache=cache)["n_p"] == 12 // best
-    prm, tile = autotune.tuned_setup(base, cache=cache)
-    assert prm["dnum"] == best and tile == next(r["tile"] for r in table if r["dnum"] == best)
+    prm, row = autotune.tuned_setup(base, cache=cache)
+    assert prm["dnum"] == best and row["tile"] == next(r["tile"] for r in table if r["dnum"] == best)
+    assert row["pass_min_blocks"] in autotune.PASS_BLOCKS and row["inner"]["words"] == 16  # N = 2^12
 
 
 def test_many_queries_deterministic_full_size():

@@ -119,3 +119,72 @@ def test_server_close_with_work_in_flight(env):
     srv.close()  # drains the queue, frees unclaimed results
     r = ctx.query(evk, "cv", cols["x"], None, OPTS12)  # the context stays usable
     assert len(r.cts()) == 1
+
+
+def test_budget_counts_results_until_taken(env):
+    """Admission counts a finished query's result ciphertexts until ppst_wait
+    hands them over: with room for one query and its result only, the second
+    query starts after the first result is taken, not when the first query
+    finishes; every result still equals the query run alone."""
+    pp, ctx, sk, evk, cols = env
+    probe = pp.Server(ctx, evk, hbm_budget=8 * GB, max_batch=4)
+    w, r = probe.estimate("kurt", cols["x"])
+    assert w > 0 and r > 0
+    wz, rz = probe.estimate("zscore", cols["long"])
+    assert rz == 3 * r  # one result ciphertext per input ciphertext (6000 rows)
+    probe.close()
+    srv = pp.Server(ctx, evk, hbm_budget=w + r + r // 2, max_batch=4)
+    t1 = srv.submit("kurt", cols["x"], None, OPTS12)
+    t2 = srv.submit("cv", cols["x"], None, OPTS12)
+    info = srv.info()
+    assert info["budget"] == w + r + r // 2 and info["running"] == 1 and info["queued"] == 1
+    deadline = time.time() + 60
+    while srv.info()["held"] == 0 and time.time() < deadline:  # the first query finishes
+        time.sleep(0.01)
+    info = srv.info()
+    assert info["held"] == r and info["running"] == 0 and info["queued"] == 1, info
+    time.sleep(0.2)
+    assert srv.info()["queued"] == 1  # still blocked: its result is not taken yet
+    r1 = srv.wait(t1)
+    r2 = srv.wait(t2)
+    info = srv.info()
+    assert info["held"] == 0 and info["reserved"] == 0 and info["running"] == 0 and info["queued"] == 0
+    same(ctx, r1, ctx.query(evk, "kurt", cols["x"], None, OPTS12))
+    same(ctx, r2, ctx.query(evk, "cv", cols["x"], None, OPTS12))
+    srv.close()
+
+
+def test_small_query_passes_a_blocked_large_one_for_a_while(env):
+    """A query that does not fit next to the running one is passed by a smaller
+    one that does, and all three complete, each equal to the query alone."""
+    pp, ctx, sk, evk, cols = env
+    probe = pp.Server(ctx, evk, hbm_budget=8 * GB, max_batch=4)
+    wl, rl = probe.estimate("zscore", cols["long"])  # three ciphertexts: larger
+    ws, rs = probe.estimate("cv", cols["x"])
+    probe.close()
+    assert wl > ws and rl == 3 * rs
+    budget = 2 * ws + 3 * rs  # two small queries fit together; the large one fits only alone
+    assert ws + wl + rl > budget >= wl + rl and 2 * (ws + rs) <= budget
+    srv = pp.Server(ctx, evk, hbm_budget=budget, max_batch=4)
+    ta = srv.submit("cv", cols["x"], None, OPTS12)
+    tb = srv.submit("zscore", cols["long"], None, OPTS12)  # blocked behind ta
+    tc = srv.submit("kurt", cols["x"], None, OPTS12)       # fits beside ta: passes tb
+    info = srv.info()
+    assert info["running"] == 2 and info["queued"] == 1, info
+    res = [srv.wait(t) for t in (ta, tb, tc)]
+    for q, r in zip((("cv", cols["x"]), ("zscore", cols["long"]), ("kurt", cols["x"])), res):
+        same(ctx, r, ctx.query(evk, q[0], q[1], None, OPTS12))
+    srv.close()
+
+
+def test_budget_from_free_device_memory(env):
+    """hbm_budget = 0 takes the device's free memory (less a 5 % reserve)."""
+    import torch
+    pp, ctx, sk, evk, cols = env
+    free, total = torch.cuda.mem_get_info()
+    srv = pp.Server(ctx, evk, hbm_budget=0, max_batch=4)
+    b = srv.info()["budget"]
+    assert 0 < b <= free + ctx.mem_info()[1] and b >= free - total // 20 - (1 << 30)
+    t = srv.submit("kurt", cols["x"], None, OPTS12)
+    same(ctx, srv.wait(t), ctx.query(evk, "kurt", cols["x"], None, OPTS12))
+    srv.close()
