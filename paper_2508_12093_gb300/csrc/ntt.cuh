@@ -41,14 +41,15 @@ struct PassShape {
     static constexpr int MIN_BLOCKS = THREADS >= 256 ? 3 : (THREADS >= 128 ? 4 : 8);
 };
 
-// COLS passes keep row p of column `sub` at (p + p / E) SUB + sub: the pad
-// word every E rows keeps both transposes free of bank conflicts for any SUB
-// (a half-warp touches 16 / SUB rows that are either consecutive or E apart)
+// COLS passes keep row p of column `sub` at p SUB + sub (SUB = 16: a half-warp
+// reads 16 columns of one row) or, for SUB < 16, at (p + p / E) SUB + sub: the
+// pad every E rows keeps both transposes free of bank conflicts (a half-warp
+// then touches 16 / SUB rows that are either consecutive or E apart)
 template <int S, int SUB>
 __device__ __forceinline__ int cols_smem(int p)
 {
     typedef PassShape<S, SUB> P;
-    return (p + p / P::E) * SUB;
+    return SUB == 16 ? p * 16 : (p + p / P::E) * SUB;
 }
 
 // forward lazy butterfly: X, Y in [0, 4q) -> [0, 4q)
