@@ -127,14 +127,15 @@ int ppst_ctx_set_tile(ppst_ctx *ctx, uint32_t inner_sub);
 /* Block shape of the transform passes (no counterpart in the paper): a pass
  * over few limbs runs 8 or 4 sub-transforms per block instead of 16 (and the
  * inner product a smaller tile than ppst_ctx_set_tile's) whenever 16 would give
- * a grid of fewer than `min_blocks` blocks (default 456 = 3 x 152 SMs; 0: always
+ * a grid of fewer than `min_blocks` blocks (default 228 = 1.5 x 152 SMs; 0: always
  * 16; 2^20: always 4). Changes speed only, never results. PPST_E_ARG above 2^20. */
 int ppst_ctx_set_pass_blocks(ppst_ctx *ctx, uint32_t min_blocks);
 /* Thread shape of the key-switching inner product (no counterpart in the
- * paper): its transform pass keeps 16 (default) or 8 words per thread (8: one
- * warp per 256-point chunk, three butterfly rounds; used at N = 2^15 and 2^16
- * only, 16 elsewhere); lazy = 1 (8 words only) accumulates the key products
- * exactly in 128 bits and reduces once per word. Speed only, never results.
+ * paper): its transform pass keeps 16 or 8 words per thread (8: one warp per
+ * 256-point chunk, three butterfly rounds; used at N = 2^15 and 2^16 only, 16
+ * elsewhere); lazy = 1 (8 words only) accumulates the key products exactly in
+ * 128 bits and reduces once per word. Default: 8 words, lazy (the fastest
+ * measured at N = 2^16). Speed only, never results.
  * PPST_E_ARG for other values. */
 int ppst_ctx_set_inner_shape(ppst_ctx *ctx, uint32_t words_per_thread, uint32_t lazy);
 /* Failure-detection self-test (no counterpart in the paper): launches one block

@@ -126,7 +126,7 @@ struct Prof {
 
 struct Ctx {
     uint32_t tag = TAG_CTX;
-    uint32_t pass_min_blocks = 456;  // transform passes: smaller blocks below this grid size (3 x 152 SMs)
+    uint32_t pass_min_blocks = 228;  // transform passes: smaller blocks below this grid size (1.5 x 152 SMs)
     Prof prof;
     ppst_params prm{};
     int logN = 0, N = 0, S = 0, L = 0, K = 0, dnum = 0, alpha = 0, np = 0;
@@ -178,8 +178,8 @@ struct Ctx {
     int ws_items = 0;
     size_t ws_bytes = 0;
     int inner_sub = 8;  // chunks per block of the key inner product (4, 8 or 16; autotuned)
-    int inner_words = 16;  // words per thread of the inner product's transform (16, or 8 at N >= 2^15)
-    bool inner_lazy = false;  // 8 words: accumulate the key products in 128 bits, reduce once
+    int inner_words = 8;     // words per thread of the inner product's transform (8 is used at N >= 2^15 only)
+    bool inner_lazy = true;  // 8 words: accumulate the key products in 128 bits, reduce once
 
     size_t ct_words() const { return (size_t)2 * (L + 1) * N; }
     size_t ext_rows() const { return (size_t)(L + 1 + K); }

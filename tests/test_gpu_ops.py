@@ -276,7 +276,7 @@ def test_pass_block_shapes_agree(env, min_blocks):
         same(ctx, ctx.rotsum(evk, ga), oc.rotsum(oa, ok))
         same(ctx, ctx.mul_const(ga, 0.37), oc.mul_const(oa, 0.37))
     finally:
-        ctx.set_pass_blocks(456)
+        ctx.set_pass_blocks(228)
     with pytest.raises(pp.PpstError) as e:
         ctx.set_pass_blocks((1 << 20) + 1)
     assert e.value.code == -1

@@ -48,9 +48,16 @@ def test_every_dnum_full_size(dnum):
         al = ctx.drop(a, lv)
         check(ctx, ctx.hmult(evk, al, b), want[("hmult", lv)], f"dnum {dnum} hmult level {lv}")
         check(ctx, ctx.rotate(evk, al, oj.ROT), want[("rot", lv)], f"dnum {dnum} rotation level {lv}")
-    for tile in (4, 16):  # the inner product's other tiles at the top level
+    # every inner-product shape (words per thread, lazy accumulation, tile) at the top level
+    for words, lazy, tile in ((16, False, 4), (16, False, 8), (16, False, 16), (8, False, 4), (8, False, 8),
+                              (8, True, 4), (8, True, 8)):
+        ctx.set_inner_shape(words, lazy)
         ctx.set_tile(tile)
-        check(ctx, ctx.hmult(evk, a, b), want[("hmult", 23)], f"dnum {dnum} hmult tile {tile}")
+        what = f"dnum {dnum}, inner {words} words, lazy {lazy}, tile {tile}"
+        check(ctx, ctx.hmult(evk, a, b), want[("hmult", 23)], what + ", hmult")
+        if words == 8:
+            check(ctx, ctx.rotate(evk, ctx.drop(a, 8), oj.ROT), want[("rot", 8)], what + ", rotation level 8")
+    ctx.set_inner_shape(8, True)
     ctx.set_tile(8)
     # the block shapes the default picks elsewhere: 4 sub-transforms per block at
     # the top level, 16 at level 1
@@ -61,18 +68,7 @@ def test_every_dnum_full_size(dnum):
     a1 = ctx.drop(a, 1)
     check(ctx, ctx.hmult(evk, a1, b), want[("hmult", 1)], f"dnum {dnum} hmult level 1, 16 per block")
     check(ctx, ctx.rotate(evk, a1, oj.ROT), want[("rot", 1)], f"dnum {dnum} rotation level 1, 16 per block")
-    ctx.set_pass_blocks(456)
-    # the inner product with 8 words per thread, plain and with 128-bit accumulation,
-    # in tiles of 8 and 4 chunks
-    for lazy in (False, True):
-        ctx.set_inner_shape(8, lazy)
-        for tile in (8, 4):
-            ctx.set_tile(tile)
-            what = f"dnum {dnum}, 8 words per thread, lazy {lazy}, tile {tile}"
-            check(ctx, ctx.hmult(evk, a, b), want[("hmult", 23)], what + ", hmult")
-            check(ctx, ctx.rotate(evk, ctx.drop(a, 8), oj.ROT), want[("rot", 8)], what + ", rotation level 8")
-    ctx.set_inner_shape(16, False)
-    ctx.set_tile(8)
+    ctx.set_pass_blocks(228)
 
 
 @pytest.mark.oracle16("batch")
