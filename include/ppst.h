@@ -133,11 +133,12 @@ int ppst_ctx_set_pass_blocks(ppst_ctx *ctx, uint32_t min_blocks);
 /* Thread shape of the key-switching inner product (no counterpart in the
  * paper): its transform pass keeps 16 or 8 words per thread (8: one warp per
  * 256-point chunk, three butterfly rounds; used at N = 2^15 and 2^16 only, 16
- * elsewhere); lazy = 1 (8 words only) accumulates the key products exactly in
- * 128 bits and reduces once per word. Default: 8 words, lazy (the fastest
- * measured at N = 2^16). Speed only, never results.
- * PPST_E_ARG for other values. */
-int ppst_ctx_set_inner_shape(ppst_ctx *ctx, uint32_t words_per_thread, uint32_t lazy);
+ * elsewhere). flags (8 words only): bit 0 accumulates the key products exactly
+ * in 128 bits and reduces once per word; bit 1 exchanges the transform's words
+ * between the rounds by warp shuffles instead of through shared memory.
+ * Default: 8 words, flags 1 (the fastest measured at N = 2^16). Speed only,
+ * never results. PPST_E_ARG for other values. */
+int ppst_ctx_set_inner_shape(ppst_ctx *ctx, uint32_t words_per_thread, uint32_t flags);
 /* Failure-detection self-test (no counterpart in the paper): launches one block
  * that waits on a shared-memory barrier nothing completes, bounded by timeout_us
  * (1 .. 10^6); like the kernels with asynchronous copies, it records the timeout

@@ -457,9 +457,11 @@ class Context:
         self.inner_sub = int(inner_sub)
 
 
-    def set_inner_shape(self, words_per_thread, lazy=False):
-        """ppst_ctx_set_inner_shape: 16 or 8 words per thread in the inner product (speed only)."""
-        self._check(lib.ppst_ctx_set_inner_shape(self.ptr, int(words_per_thread), int(bool(lazy))))
+    def set_inner_shape(self, words_per_thread, lazy=False, shuffle=False):
+        """ppst_ctx_set_inner_shape: 16 or 8 words per thread in the inner product, lazy 128-bit
+        accumulation and warp-shuffle exchanges (8 words only); speed only."""
+        flags = int(bool(lazy)) | (2 if shuffle else 0)
+        self._check(lib.ppst_ctx_set_inner_shape(self.ptr, int(words_per_thread), flags))
 
     def set_pass_blocks(self, min_blocks):
         """ppst_ctx_set_pass_blocks: smaller transform blocks below this grid size (speed only)."""

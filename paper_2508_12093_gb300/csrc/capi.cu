@@ -103,15 +103,16 @@ int ppst_ctx_set_tile(ppst_ctx *ctx, uint32_t inner_sub)
     });
 }
 
-int ppst_ctx_set_inner_shape(ppst_ctx *ctx, uint32_t words_per_thread, uint32_t lazy)
+int ppst_ctx_set_inner_shape(ppst_ctx *ctx, uint32_t words_per_thread, uint32_t flags)
 {
     Ctx *c = (Ctx *)ctx;
     if (!ok(c, TAG_CTX)) return PPST_E_ARG;
     return guard(c, [&] {
         REQ(words_per_thread == 8 || words_per_thread == 16, "words_per_thread must be 8 or 16");
-        REQ(lazy <= 1 && (lazy == 0 || words_per_thread == 8), "lazy accumulation needs 8 words per thread");
+        REQ(flags <= 3 && (flags == 0 || words_per_thread == 8), "flags need 8 words per thread");
         c->inner_words = (int)words_per_thread;
-        c->inner_lazy = lazy != 0;
+        c->inner_lazy = (flags & 1) != 0;
+        c->inner_shfl = (flags & 2) != 0;
     });
 }
 

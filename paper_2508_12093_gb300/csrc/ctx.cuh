@@ -180,6 +180,7 @@ struct Ctx {
     int inner_sub = 8;  // chunks per block of the key inner product (4, 8 or 16; autotuned)
     int inner_words = 8;     // words per thread of the inner product's transform (8 is used at N >= 2^15 only)
     bool inner_lazy = true;  // 8 words: accumulate the key products in 128 bits, reduce once
+    bool inner_shfl = false; // 8 words: the transform's exchanges by warp shuffles instead of shared memory
 
     size_t ct_words() const { return (size_t)2 * (L + 1) * N; }
     size_t ext_rows() const { return (size_t)(L + 1 + K); }

@@ -295,7 +295,56 @@ __device__ __forceinline__ int swz8(int p) { return p ^ ((p >> 4) & 7) ^ (((p >>
 // (the 16-word storage order of ntt.cuh: E h + k -> h + 16 k)
 __device__ __forceinline__ int addr16(int p) { return (p >> 4) + ((p & 15) << 4); }
 
-// forward CHUNKS pass of chunk g, 8 words per thread: words h + 32 k in, 8 h + k out
+// The two exchanges by warp shuffles instead of shared memory (a variant the
+// autotuner measures). A -> B swaps lane bits 2..4 with register bits 0..2
+// (three butterfly-pattern rounds of shfl.xor 4, 8, 16); B -> C transposes, for
+// each register parity, lane bits 0..1 with register bits 1..2 (rounds 1, 2).
+// Each round sends the half of the registers the partner needs and keeps the rest.
+__device__ __forceinline__ void xchg_ab_shfl(uint64_t (&x)[8], int h)
+{
+#pragma unroll
+    for (int bit = 0; bit < 3; bit++) {
+        const int s = 4 << bit, sv = 1 << bit;
+        const bool up = h & s;
+#pragma unroll
+        for (int a = 0; a < 8; a++) {
+            if (a & sv) continue;
+            const uint64_t send = up ? x[a] : x[a | sv];
+            const uint64_t recv = __shfl_xor_sync(0xffffffffu, send, s);
+            if (up) x[a] = recv;
+            else x[a | sv] = recv;
+        }
+    }
+}
+
+__device__ __forceinline__ void xchg_bc_shfl(uint64_t (&x)[8], int h)
+{
+    uint64_t y[8];
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+        uint64_t m[4] = {x[b], x[2 + b], x[4 + b], x[6 + b]};
+#pragma unroll
+        for (int s = 1; s <= 2; s <<= 1) {
+            const bool up = h & s;
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                if (a & s) continue;
+                const uint64_t send = up ? m[a] : m[a | s];
+                const uint64_t recv = __shfl_xor_sync(0xffffffffu, send, s);
+                if (up) m[a] = recv;
+                else m[a | s] = recv;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++) y[r + 4 * b] = m[r];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = y[k];
+}
+
+// forward CHUNKS pass of chunk g, 8 words per thread: words h + 32 k in, 8 h + k out;
+// the exchanges go through the warp's shared-memory buffer `ex` or (SHFL) through shuffles
+template <bool SHFL>
 __device__ __forceinline__ void chunks_fwd_core8(uint64_t (&x)[8], uint64_t *ex, int h, int g, int N,
                                                  const Tw *__restrict__ T, uint64_t q)
 {
@@ -310,13 +359,17 @@ __device__ __forceinline__ void chunks_fwd_core8(uint64_t (&x)[8], uint64_t *ex,
             bfly_fwd(x[k], x[k + (1 << s)], ldtw(T + base + (k >> (s + 1))), q, q2);
         }
     }
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < 8; k++) ex[swz8(h + 32 * k)] = x[k];
-    __syncwarp();
     const int hh = h >> 2, hl = h & 3;
+    if (SHFL) {
+        xchg_ab_shfl(x, h);
+    } else {
+        __syncwarp();
 #pragma unroll
-    for (int k = 0; k < 8; k++) x[k] = ex[swz8(32 * hh + 4 * k + hl)];
+        for (int k = 0; k < 8; k++) ex[swz8(h + 32 * k)] = x[k];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) x[k] = ex[swz8(32 * hh + 4 * k + hl)];
+    }
 #pragma unroll
     for (int s = 2; s >= 0; s--) {  // d = 4 << s: group p / 2d = (hh << (2 - s)) | (k >> (s + 1))
         const int d = 4 << s;
@@ -327,12 +380,16 @@ __device__ __forceinline__ void chunks_fwd_core8(uint64_t (&x)[8], uint64_t *ex,
             bfly_fwd(x[k], x[k + (1 << s)], ldtw(T + base + (k >> (s + 1))), q, q2);
         }
     }
-    __syncwarp();
+    if (SHFL) {
+        xchg_bc_shfl(x, h);
+    } else {
+        __syncwarp();
 #pragma unroll
-    for (int k = 0; k < 8; k++) ex[swz8(32 * hh + 4 * k + hl)] = x[k];
-    __syncwarp();
+        for (int k = 0; k < 8; k++) ex[swz8(32 * hh + 4 * k + hl)] = x[k];
+        __syncwarp();
 #pragma unroll
-    for (int k = 0; k < 8; k++) x[k] = ex[swz8(8 * h + k)];
+        for (int k = 0; k < 8; k++) x[k] = ex[swz8(8 * h + k)];
+    }
 #pragma unroll
     for (int s = 1; s >= 0; s--) {  // d = 1 << s: group (8 h + k) / 2d
         const int d = 1 << s;
@@ -345,7 +402,7 @@ __device__ __forceinline__ void chunks_fwd_core8(uint64_t (&x)[8], uint64_t *ex,
     }
 }
 
-template <int SUB, bool LAZY>
+template <int SUB, bool LAZY, bool SHFL>
 __global__ void __launch_bounds__(Inner8Smem<SUB>::THREADS, SUB == 8 ? 2 : 4)
     k_inner8(const uint64_t *__restrict__ ext, const uint64_t *__restrict__ d2n, const uint64_t *__restrict__ key,
              uint64_t *__restrict__ acc, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN, int level,
@@ -409,7 +466,7 @@ __global__ void __launch_bounds__(Inner8Smem<SUB>::THREADS, SUB == 8 ? 2 : 4)
         } else {
 #pragma unroll
             for (int k = 0; k < 8; k++) x[k] = xt[sub * SM::M + h + 32 * k];
-            chunks_fwd_core8(x, ex, h, g, N, T, p.q);
+            chunks_fwd_core8<SHFL>(x, ex, h, g, N, T, p.q);
 #pragma unroll
             for (int k = 0; k < 8; k++) x[k] = reduce4q(x[k], p.q);
         }
@@ -530,19 +587,23 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
         launch_on(c, k_inner_chunks<S, SUB>, grid, SM::THREADS, SM::BYTES, c.ws_ext, c.ws_d2n, key.d, c.ws_acc,
             c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, B, ws, c.d_err);
     };
-    auto launch8 = [&](auto subv, auto lazyv) {
+    auto launch8s = [&](auto subv, auto lazyv, auto shflv) {
         constexpr int SUB = decltype(subv)::value;
-        constexpr bool LAZY = decltype(lazyv)::value;
+        constexpr bool LAZY = decltype(lazyv)::value, SHFL = decltype(shflv)::value;
         typedef Inner8Smem<SUB> SM;
         const dim3 grid(B * (c.N / SM::TILE), E_ext);
         static std::atomic<bool> attr_set{false};
         if (!attr_set.load()) {
-            PPST_CUDA(cudaFuncSetAttribute(k_inner8<SUB, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            PPST_CUDA(cudaFuncSetAttribute(k_inner8<SUB, LAZY, SHFL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)SM::BYTES));
             attr_set = true;
         }
-        launch_on(c, k_inner8<SUB, LAZY>, grid, SM::THREADS, SM::BYTES, c.ws_ext, c.ws_d2n, key.d, c.ws_acc,
-            c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, B, ws, c.d_err);
+        launch_on(c, k_inner8<SUB, LAZY, SHFL>, grid, SM::THREADS, SM::BYTES, c.ws_ext, c.ws_d2n, key.d,
+            c.ws_acc, c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, B, ws, c.d_err);
+    };
+    auto launch8 = [&](auto subv, auto lazyv) {
+        if (c.inner_shfl) launch8s(subv, lazyv, std::true_type{});
+        else launch8s(subv, lazyv, std::false_type{});
     };
     dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;

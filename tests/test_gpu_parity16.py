@@ -49,11 +49,12 @@ def test_every_dnum_full_size(dnum):
         check(ctx, ctx.hmult(evk, al, b), want[("hmult", lv)], f"dnum {dnum} hmult level {lv}")
         check(ctx, ctx.rotate(evk, al, oj.ROT), want[("rot", lv)], f"dnum {dnum} rotation level {lv}")
     # every inner-product shape (words per thread, lazy accumulation, tile) at the top level
-    for words, lazy, tile in ((16, False, 4), (16, False, 8), (16, False, 16), (8, False, 4), (8, False, 8),
-                              (8, True, 4), (8, True, 8)):
-        ctx.set_inner_shape(words, lazy)
+    for words, lazy, shfl, tile in ((16, False, False, 4), (16, False, False, 8), (16, False, False, 16),
+                                    (8, False, False, 4), (8, False, False, 8), (8, True, False, 4),
+                                    (8, True, False, 8), (8, True, True, 4), (8, False, True, 8)):
+        ctx.set_inner_shape(words, lazy, shfl)
         ctx.set_tile(tile)
-        what = f"dnum {dnum}, inner {words} words, lazy {lazy}, tile {tile}"
+        what = f"dnum {dnum}, inner {words} words, lazy {lazy}, shuffle {shfl}, tile {tile}"
         check(ctx, ctx.hmult(evk, a, b), want[("hmult", 23)], what + ", hmult")
         if words == 8:
             check(ctx, ctx.rotate(evk, ctx.drop(a, 8), oj.ROT), want[("rot", 8)], what + ", rotation level 8")
