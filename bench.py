@@ -46,6 +46,7 @@ HMULT_BYTES = (2 * 2 * 24 + 6 * 2 * 28 + 2 * 24) * 65536 * 8
 # Filled in from the capture of the kernel as it now stands (empty: none yet).
 DRAM_PER_FUSED = {}
 DRAM_SOURCE = None
+# (filled from profiles/ once the final kernel has been captured)
 
 
 def peaks():
@@ -438,8 +439,10 @@ def main():
     # per batched launch; input / output ciphertexts elsewhere), not the
     # intermediates the fused kernels exchange (the library counts both per launch)
     peak, peak_kind = peaks()
-    alg_bytes = munits_dom * 8 * ctx.N
     fused_bytes = units_dom * 8 * ctx.N
+    # a class that moves no operand of the method itself (ModUp: intermediates only)
+    # falls back to its own reads-once-plus-writes, and says so
+    alg_bytes = munits_dom * 8 * ctx.N if munits_dom else fused_bytes
     achieved = (alg_bytes / (ms_dom / 1000.0)) / 1e9 if ms_dom > 0 else None
 
     # HMult + key switch microbenchmark (top level, dnum = 6)
@@ -544,7 +547,9 @@ def main():
                          "launches": n_dom, "avg_launch_us": 1000.0 * ms_dom / max(1, n_dom),
                          "share_of_step": shares[dom] / tot,
                          "algorithmic_bytes_per_launch": alg_bytes / max(1, n_dom),
-                         "algorithmic_bytes": "the switching key's limbs, once per batched launch (method operands)",
+                         "algorithmic_bytes": ("the method's operands the kernel moves: for the inner product the "
+                                               "switching key's limbs, once per batched launch" if munits_dom else
+                                               "no method operands: the limbs the kernel reads once plus writes"),
                          "fused_kernel_bytes_per_launch": fused_bytes / max(1, n_dom)},
             "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -148,6 +148,36 @@ __host__ __device__ __forceinline__ void mac(Acc128 &acc, uint64_t a, uint64_t b
 #endif
 }
 
+#ifdef __CUDACC__
+// a 128-bit accumulator kept as four 32-bit words on the device, so that a
+// chain of multiply-accumulates never repacks 64-bit halves between steps
+struct Acc4 {
+    uint32_t w0, w1, w2, w3;
+};
+__device__ __forceinline__ void mac4(Acc4 &a, uint64_t x, uint64_t y)
+{
+    asm("{\n\t"
+        ".reg .u32 x0, x1, y0, y1;\n\t"
+        "mov.b64 {x0, x1}, %4;\n\t"
+        "mov.b64 {y0, y1}, %5;\n\t"
+        "mad.lo.cc.u32 %0, x0, y0, %0;\n\t"   // + x0 y0 + x1 y1 2^64
+        "madc.hi.cc.u32 %1, x0, y0, %1;\n\t"
+        "madc.lo.cc.u32 %2, x1, y1, %2;\n\t"
+        "madc.hi.u32 %3, x1, y1, %3;\n\t"
+        "mad.lo.cc.u32 %1, x0, y1, %1;\n\t"   // + x0 y1 2^32
+        "madc.hi.cc.u32 %2, x0, y1, %2;\n\t"
+        "addc.u32 %3, %3, 0;\n\t"
+        "mad.lo.cc.u32 %1, x1, y0, %1;\n\t"   // + x1 y0 2^32
+        "madc.hi.cc.u32 %2, x1, y0, %2;\n\t"
+        "addc.u32 %3, %3, 0;\n\t"
+        "}"
+        : "+r"(a.w0), "+r"(a.w1), "+r"(a.w2), "+r"(a.w3)
+        : "l"(x), "l"(y));
+}
+__device__ __forceinline__ uint64_t acc4_lo(const Acc4 &a) { return ((uint64_t)a.w1 << 32) | a.w0; }
+__device__ __forceinline__ uint64_t acc4_hi(const Acc4 &a) { return ((uint64_t)a.w3 << 32) | a.w2; }
+#endif
+
 // ---------------------------------------------------------------------------
 // ChaCha20 block function (RFC 8439 Sec. 2.3), keyed by SplitMix64 of a seed.
 // Used on the host (secret key) and in the sampling kernels.

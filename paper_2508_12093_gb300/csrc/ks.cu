@@ -452,9 +452,13 @@ __global__ void __launch_bounds__(Inner8Smem<SUB>::THREADS, SUB == 8 ? 2 : 4)
     int ka[8];  // tile offsets (storage order) of this thread's output words 8 h + k
 #pragma unroll
     for (int k = 0; k < 8; k++) ka[k] = sub * SM::M + addr16(8 * h + k);
-    uint64_t a0[8], a1[8], b0[8], b1[8];  // LAZY: (lo, hi) = (a, b); else a only
+    uint64_t a0[8], a1[8];  // running sums (not LAZY)
+    Acc4 u0[8], u1[8];      // LAZY: exact 128-bit sums
 #pragma unroll
-    for (int k = 0; k < 8; k++) a0[k] = a1[k] = b0[k] = b1[k] = 0;
+    for (int k = 0; k < 8; k++) {
+        a0[k] = a1[k] = 0;
+        u0[k] = u1[k] = Acc4{0, 0, 0, 0};
+    }
     int j = 0;
     for (; j < nd; j++) {
         if (__syncthreads_or(!mbar_wait(&bar[j & 1], (j >> 1) & 1))) break;
@@ -475,13 +479,8 @@ __global__ void __launch_bounds__(Inner8Smem<SUB>::THREADS, SUB == 8 ? 2 : 4)
         for (int k = 0; k < 8; k++) {
             const uint64_t k0 = ks[ka[k]], k1 = ks[SM::TILE + ka[k]];
             if (LAZY) {
-                Acc128 u{a0[k], b0[k]}, v{a1[k], b1[k]};
-                mac(u, x[k], k0);
-                mac(v, x[k], k1);
-                a0[k] = u.lo;
-                b0[k] = u.hi;
-                a1[k] = v.lo;
-                b1[k] = v.hi;
+                mac4(u0[k], x[k], k0);
+                mac4(u1[k], x[k], k1);
             } else {
                 a0[k] = add_mod(a0[k], mont_mul(x[k], k0, p.q, p.qinv), p.q);
                 a1[k] = add_mod(a1[k], mont_mul(x[k], k1, p.q, p.qinv), p.q);
@@ -506,10 +505,10 @@ __global__ void __launch_bounds__(Inner8Smem<SUB>::THREADS, SUB == 8 ? 2 : 4)
 #pragma unroll
     for (int k = 0; k < 8; k++) {
         if (LAZY) {  // (hi mod q) 2^64 + lo, then one Montgomery reduction
-            const uint64_t h0 = csub(shoup(b0[k], 1, p.w64, p.q), p.q);
-            const uint64_t h1 = csub(shoup(b1[k], 1, p.w64, p.q), p.q);
-            o0[ka[k]] = mont_redc(h0, a0[k], p.q, p.qinv);
-            o1[ka[k]] = mont_redc(h1, a1[k], p.q, p.qinv);
+            const uint64_t h0 = csub(shoup(acc4_hi(u0[k]), 1, p.w64, p.q), p.q);
+            const uint64_t h1 = csub(shoup(acc4_hi(u1[k]), 1, p.w64, p.q), p.q);
+            o0[ka[k]] = mont_redc(h0, acc4_lo(u0[k]), p.q, p.qinv);
+            o1[ka[k]] = mont_redc(h1, acc4_lo(u1[k]), p.q, p.qinv);
         } else {
             o0[ka[k]] = a0[k];
             o1[ka[k]] = a1[k];

@@ -44,19 +44,19 @@ __device__ __forceinline__ void bconv_words(uint64_t (&x)[E], const uint64_t *__
 #pragma unroll
         for (int k = 0; k < E; k++) {
             const size_t pos = (size_t)(h + T * k) * C;
-            Acc128 acc{0, 0};
+            Acc4 acc{0, 0, 0, 0};
 #pragma unroll
-            for (int i = 0; i < A; i++) mac(acc, src[(size_t)i * N + pos], fr[i]);
-            x[k] = mont_redc(acc.hi, acc.lo, pt.q, pt.qinv);
+            for (int i = 0; i < A; i++) mac4(acc, src[(size_t)i * N + pos], fr[i]);
+            x[k] = mont_redc(acc4_hi(acc), acc4_lo(acc), pt.q, pt.qinv);
         }
     } else {
 #pragma unroll
         for (int k = 0; k < E; k++) {
             const size_t pos = (size_t)(h + T * k) * C;
-            Acc128 acc{0, 0};
+            Acc4 acc{0, 0, 0, 0};
 #pragma unroll 1
-            for (int i = 0; i < a; i++) mac(acc, src[(size_t)i * N + pos], f[i]);
-            x[k] = mont_redc(acc.hi, acc.lo, pt.q, pt.qinv);
+            for (int i = 0; i < a; i++) mac4(acc, src[(size_t)i * N + pos], f[i]);
+            x[k] = mont_redc(acc4_hi(acc), acc4_lo(acc), pt.q, pt.qinv);
         }
     }
 }
