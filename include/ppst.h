@@ -121,7 +121,7 @@ int ppst_ctx_create(const ppst_params *params, const ppst_allocator *alloc, void
                     ppst_ctx **out);
 const char *ppst_last_error(const ppst_ctx *ctx);
 /* Tile of the key-switching inner product (no counterpart in the paper): the
- * transform chunks each block owns, 4, 8 (default) or 16 (PPST_E_ARG
+ * transform chunks each block owns, 4 (default), 8 or 16 (PPST_E_ARG
  * otherwise). Changes speed only, never results; the autotuner measures it. */
 int ppst_ctx_set_tile(ppst_ctx *ctx, uint32_t inner_sub);
 /* Block shape of the transform passes (no counterpart in the paper): a pass

@@ -177,7 +177,7 @@ struct Ctx {
     uint64_t *ws_top = nullptr;  // [2][N]
     int ws_items = 0;
     size_t ws_bytes = 0;
-    int inner_sub = 8;  // chunks per block of the key inner product (4, 8 or 16; autotuned)
+    int inner_sub = 4;  // chunks per block of the key inner product (4, 8 or 16; autotuned)
     int inner_words = 8;     // words per thread of the inner product's transform (8 is used at N >= 2^15 only)
     bool inner_lazy = true;  // 8 words: accumulate the key products in 128 bits, reduce once
     bool inner_shfl = false; // 8 words: the transform's exchanges by warp shuffles instead of shared memory

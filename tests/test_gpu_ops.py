@@ -253,7 +253,7 @@ def test_inner_product_tiles_agree(env, tile):
         same(ctx, ctx.hmult(evk, ga, ga), oc.hmult(oa, oa, ok))
         same(ctx, ctx.rotate(evk, ga, 4), oc.rotate(oa, 4, ok))
     finally:
-        ctx.set_tile(8)
+        ctx.set_tile(4)
     with pytest.raises(pp.PpstError) as e:
         ctx.set_tile(5)
     assert e.value.code == -1

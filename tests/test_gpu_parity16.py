@@ -59,7 +59,7 @@ def test_every_dnum_full_size(dnum):
         if words == 8:
             check(ctx, ctx.rotate(evk, ctx.drop(a, 8), oj.ROT), want[("rot", 8)], what + ", rotation level 8")
     ctx.set_inner_shape(8, True)
-    ctx.set_tile(8)
+    ctx.set_tile(4)
     # the block shapes the default picks elsewhere: 4 sub-transforms per block at
     # the top level, 16 at level 1
     ctx.set_pass_blocks(1 << 20)
