@@ -283,7 +283,8 @@ struct Inner8Smem {
     static constexpr size_t X_OFF = 128;                              // two digit tiles
     static constexpr size_t K_OFF = X_OFF + 2 * (size_t)TILE * 8;    // two key tiles
     static constexpr size_t T_OFF = K_OFF + 2 * (size_t)TILE * 8;    // exchange buffers
-    static constexpr size_t BYTES = T_OFF + (size_t)TILE * 8;
+    static constexpr size_t W_OFF = T_OFF + (size_t)TILE * 8;        // the chunks' twiddles (255 each)
+    static constexpr size_t BYTES = W_OFF + (size_t)SUB * M * sizeof(Tw);
 };
 
 // XOR swizzle of a chunk's 256 words: the three layouts a warp uses (h + 32 k,
@@ -342,21 +343,20 @@ __device__ __forceinline__ void xchg_bc_shfl(uint64_t (&x)[8], int h)
     for (int k = 0; k < 8; k++) x[k] = y[k];
 }
 
-// forward CHUNKS pass of chunk g, 8 words per thread: words h + 32 k in, 8 h + k out;
-// the exchanges go through the warp's shared-memory buffer `ex` or (SHFL) through shuffles
-template <bool SHFL>
-__device__ __forceinline__ void chunks_fwd_core8(uint64_t (&x)[8], uint64_t *ex, int h, int g, int N,
-                                                 const Tw *__restrict__ T, uint64_t q)
+// forward CHUNKS pass of a chunk, 8 words per thread: words h + 32 k in, 8 h + k out;
+// the exchanges go through the warp's shared-memory buffer `ex` or (SHFL) through
+// shuffles. tw(m, j) is the twiddle of group j of the stage with m groups per chunk
+// (distance 128 / m): psi^brv of m (N / 256 + g) + j for chunk g.
+template <bool SHFL, class TwF>
+__device__ __forceinline__ void chunks_fwd_core8(uint64_t (&x)[8], uint64_t *ex, int h, TwF &&tw, uint64_t q)
 {
     const uint64_t q2 = 2 * q;
 #pragma unroll
-    for (int s = 2; s >= 0; s--) {  // d = 32 << s: group (h + 32 k) / 2d = k >> (s + 1)
-        const int d = 32 << s;
-        const int base = N / (2 * d) + g * (256 / (2 * d));
+    for (int s = 2; s >= 0; s--) {  // distance 32 << s: m = 4 >> s groups, group k >> (s + 1)
 #pragma unroll
         for (int k = 0; k < 8; k++) {
             if ((k >> s) & 1) continue;
-            bfly_fwd(x[k], x[k + (1 << s)], ldtw(T + base + (k >> (s + 1))), q, q2);
+            bfly_fwd(x[k], x[k + (1 << s)], tw(4 >> s, k >> (s + 1)), q, q2);
         }
     }
     const int hh = h >> 2, hl = h & 3;
@@ -371,13 +371,11 @@ __device__ __forceinline__ void chunks_fwd_core8(uint64_t (&x)[8], uint64_t *ex,
         for (int k = 0; k < 8; k++) x[k] = ex[swz8(32 * hh + 4 * k + hl)];
     }
 #pragma unroll
-    for (int s = 2; s >= 0; s--) {  // d = 4 << s: group p / 2d = (hh << (2 - s)) | (k >> (s + 1))
-        const int d = 4 << s;
-        const int base = N / (2 * d) + g * (256 / (2 * d)) + (hh << (2 - s));
+    for (int s = 2; s >= 0; s--) {  // distance 4 << s: m = 32 >> s, group (hh << (2 - s)) | (k >> (s + 1))
 #pragma unroll
         for (int k = 0; k < 8; k++) {
             if ((k >> s) & 1) continue;
-            bfly_fwd(x[k], x[k + (1 << s)], ldtw(T + base + (k >> (s + 1))), q, q2);
+            bfly_fwd(x[k], x[k + (1 << s)], tw(32 >> s, (hh << (2 - s)) | (k >> (s + 1))), q, q2);
         }
     }
     if (SHFL) {
@@ -391,13 +389,11 @@ __device__ __forceinline__ void chunks_fwd_core8(uint64_t (&x)[8], uint64_t *ex,
         for (int k = 0; k < 8; k++) x[k] = ex[swz8(8 * h + k)];
     }
 #pragma unroll
-    for (int s = 1; s >= 0; s--) {  // d = 1 << s: group (8 h + k) / 2d
-        const int d = 1 << s;
-        const int base = N / (2 * d) + g * (256 / (2 * d));
+    for (int s = 1; s >= 0; s--) {  // distance 1 << s: m = 128 >> s, group (8 h + k) >> (s + 1)
 #pragma unroll
         for (int k = 0; k < 8; k++) {
             if ((k >> s) & 1) continue;
-            bfly_fwd(x[k], x[k + d], ldtw(T + base + ((8 * h + k) >> (s + 1))), q, q2);
+            bfly_fwd(x[k], x[k + (1 << s)], tw(128 >> s, (8 * h + k) >> (s + 1)), q, q2);
         }
     }
 }
@@ -447,8 +443,19 @@ __global__ void __launch_bounds__(Inner8Smem<SUB>::THREADS, SUB == 8 ? 2 : 4)
     }
     __syncthreads();
     const int h = threadIdx.x & 31, sub = threadIdx.x >> 5;
-    const int g = tile * SUB + sub;
     uint64_t *ex = reinterpret_cast<uint64_t *>(smem + SM::T_OFF) + sub * SM::M;
+    // the 255 twiddles each chunk's pass uses (entry m + j: group j of the stage with
+    // m groups), loaded once and reused by every digit: entry i of chunk c is
+    // psi^brv of m (N / 256 + g_c) + (i - m), m the largest power of two <= i
+    Tw *twc = reinterpret_cast<Tw *>(smem + SM::W_OFF);
+    for (int i = threadIdx.x; i < SUB * SM::M; i += SM::THREADS) {
+        const int c = i >> 8, e = i & 255;
+        if (e == 0) continue;
+        const int m = 1 << (31 - __clz(e));
+        twc[i] = ldtw(T + (size_t)m * ((N >> 8) + tile * SUB + c) + (e - m));
+    }
+    __syncthreads();
+    const Tw *tc = twc + sub * SM::M;
     int ka[8];  // tile offsets (storage order) of this thread's output words 8 h + k
 #pragma unroll
     for (int k = 0; k < 8; k++) ka[k] = sub * SM::M + addr16(8 * h + k);
@@ -470,7 +477,7 @@ __global__ void __launch_bounds__(Inner8Smem<SUB>::THREADS, SUB == 8 ? 2 : 4)
         } else {
 #pragma unroll
             for (int k = 0; k < 8; k++) x[k] = xt[sub * SM::M + h + 32 * k];
-            chunks_fwd_core8<SHFL>(x, ex, h, g, N, T, p.q);
+            chunks_fwd_core8<SHFL>(x, ex, h, [&](int m, int jj) { return tc[m + jj]; }, p.q);
 #pragma unroll
             for (int k = 0; k < 8; k++) x[k] = reduce4q(x[k], p.q);
         }
