@@ -66,25 +66,22 @@ __host__ __device__ __forceinline__ uint64_t mont_redc(uint64_t hi, uint64_t lo,
 __host__ __device__ __forceinline__ void mul128(uint64_t a, uint64_t b, uint64_t &lo, uint64_t &hi)
 {
 #ifdef __CUDA_ARCH__
-    asm("{\n\t"
-        ".reg .u32 a0, a1, b0, b1, w0, w1, w2, w3;\n\t"
-        "mov.b64 {a0, a1}, %2;\n\t"
-        "mov.b64 {b0, b1}, %3;\n\t"
-        "mul.lo.u32 w0, a0, b0;\n\t"
-        "mul.hi.u32 w1, a0, b0;\n\t"
-        "mul.lo.u32 w2, a1, b1;\n\t"
-        "mul.hi.u32 w3, a1, b1;\n\t"
-        "mad.lo.cc.u32 w1, a0, b1, w1;\n\t"
-        "madc.hi.cc.u32 w2, a0, b1, w2;\n\t"
-        "addc.u32 w3, w3, 0;\n\t"
-        "mad.lo.cc.u32 w1, a1, b0, w1;\n\t"
-        "madc.hi.cc.u32 w2, a1, b0, w2;\n\t"
-        "addc.u32 w3, w3, 0;\n\t"
-        "mov.b64 %0, {w0, w1};\n\t"
-        "mov.b64 %1, {w2, w3};\n\t"
-        "}"
-        : "=l"(lo), "=l"(hi)
-        : "l"(a), "l"(b));
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    uint32_t w0, w1, w2, w3;
+    asm("mul.lo.u32 %0, %4, %6;\n\t"
+        "mul.hi.u32 %1, %4, %6;\n\t"
+        "mul.lo.u32 %2, %5, %7;\n\t"
+        "mul.hi.u32 %3, %5, %7;\n\t"
+        "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"
+        "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+        "addc.u32 %3, %3, 0;\n\t"
+        "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
+        "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "=r"(w0), "=r"(w1), "=r"(w2), "=r"(w3)
+        : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+    lo = ((uint64_t)w1 << 32) | w0;
+    hi = ((uint64_t)w3 << 32) | w2;
 #else
     lo = a * b;
     hi = mulhi64(a, b);
@@ -115,31 +112,30 @@ struct Acc128 {
 // acc += a b (mod 2^128). On the device the four 32 x 32-bit partial products
 // are accumulated straight into the four 32-bit words of acc with carry chains
 // (schoolbook multiplication): no separate 64-bit high and low products, which
-// would each recompute the cross terms.
+// would each recompute the cross terms. Operands enter as their 32-bit halves
+// (the halves of a 64-bit register pair, so no moves are needed).
+#define PPST_MAC4_ASM                                                                   \
+    "mad.lo.cc.u32 %0, %4, %6, %0;\n\t"   /* + a0 b0 + a1 b1 2^64 */                  \
+    "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"                                              \
+    "madc.lo.cc.u32 %2, %5, %7, %2;\n\t"                                              \
+    "madc.hi.u32 %3, %5, %7, %3;\n\t"                                                 \
+    "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"   /* + a0 b1 2^32 */                          \
+    "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"                                              \
+    "addc.u32 %3, %3, 0;\n\t"                                                         \
+    "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"   /* + a1 b0 2^32 */                          \
+    "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"                                              \
+    "addc.u32 %3, %3, 0;"
+
 __host__ __device__ __forceinline__ void mac(Acc128 &acc, uint64_t a, uint64_t b)
 {
 #ifdef __CUDA_ARCH__
-    asm("{\n\t"
-        ".reg .u32 a0, a1, b0, b1, w0, w1, w2, w3;\n\t"
-        "mov.b64 {a0, a1}, %2;\n\t"
-        "mov.b64 {b0, b1}, %3;\n\t"
-        "mov.b64 {w0, w1}, %0;\n\t"
-        "mov.b64 {w2, w3}, %1;\n\t"
-        "mad.lo.cc.u32 w0, a0, b0, w0;\n\t"   // + a0 b0 + a1 b1 2^64
-        "madc.hi.cc.u32 w1, a0, b0, w1;\n\t"
-        "madc.lo.cc.u32 w2, a1, b1, w2;\n\t"
-        "madc.hi.u32 w3, a1, b1, w3;\n\t"
-        "mad.lo.cc.u32 w1, a0, b1, w1;\n\t"   // + a0 b1 2^32
-        "madc.hi.cc.u32 w2, a0, b1, w2;\n\t"
-        "addc.u32 w3, w3, 0;\n\t"
-        "mad.lo.cc.u32 w1, a1, b0, w1;\n\t"   // + a1 b0 2^32
-        "madc.hi.cc.u32 w2, a1, b0, w2;\n\t"
-        "addc.u32 w3, w3, 0;\n\t"
-        "mov.b64 %0, {w0, w1};\n\t"
-        "mov.b64 %1, {w2, w3};\n\t"
-        "}"
-        : "+l"(acc.lo), "+l"(acc.hi)
-        : "l"(a), "l"(b));
+    uint32_t w0 = (uint32_t)acc.lo, w1 = (uint32_t)(acc.lo >> 32), w2 = (uint32_t)acc.hi,
+             w3 = (uint32_t)(acc.hi >> 32);
+    asm(PPST_MAC4_ASM
+        : "+r"(w0), "+r"(w1), "+r"(w2), "+r"(w3)
+        : "r"((uint32_t)a), "r"((uint32_t)(a >> 32)), "r"((uint32_t)b), "r"((uint32_t)(b >> 32)));
+    acc.lo = ((uint64_t)w1 << 32) | w0;
+    acc.hi = ((uint64_t)w3 << 32) | w2;
 #else
     uint64_t l = a * b;
     uint64_t h = mulhi64(a, b);
@@ -156,23 +152,9 @@ struct Acc4 {
 };
 __device__ __forceinline__ void mac4(Acc4 &a, uint64_t x, uint64_t y)
 {
-    asm("{\n\t"
-        ".reg .u32 x0, x1, y0, y1;\n\t"
-        "mov.b64 {x0, x1}, %4;\n\t"
-        "mov.b64 {y0, y1}, %5;\n\t"
-        "mad.lo.cc.u32 %0, x0, y0, %0;\n\t"   // + x0 y0 + x1 y1 2^64
-        "madc.hi.cc.u32 %1, x0, y0, %1;\n\t"
-        "madc.lo.cc.u32 %2, x1, y1, %2;\n\t"
-        "madc.hi.u32 %3, x1, y1, %3;\n\t"
-        "mad.lo.cc.u32 %1, x0, y1, %1;\n\t"   // + x0 y1 2^32
-        "madc.hi.cc.u32 %2, x0, y1, %2;\n\t"
-        "addc.u32 %3, %3, 0;\n\t"
-        "mad.lo.cc.u32 %1, x1, y0, %1;\n\t"   // + x1 y0 2^32
-        "madc.hi.cc.u32 %2, x1, y0, %2;\n\t"
-        "addc.u32 %3, %3, 0;\n\t"
-        "}"
+    asm(PPST_MAC4_ASM
         : "+r"(a.w0), "+r"(a.w1), "+r"(a.w2), "+r"(a.w3)
-        : "l"(x), "l"(y));
+        : "r"((uint32_t)x), "r"((uint32_t)(x >> 32)), "r"((uint32_t)y), "r"((uint32_t)(y >> 32)));
 }
 __device__ __forceinline__ uint64_t acc4_lo(const Acc4 &a) { return ((uint64_t)a.w1 << 32) | a.w0; }
 __device__ __forceinline__ uint64_t acc4_hi(const Acc4 &a) { return ((uint64_t)a.w3 << 32) | a.w2; }
