@@ -133,9 +133,11 @@ int ppst_ctx_set_pass_blocks(ppst_ctx *ctx, uint32_t min_blocks);
 /* Thread shape of the key-switching inner product (no counterpart in the
  * paper): its transform pass keeps 16 or 8 words per thread (8: one warp per
  * 256-point chunk, three butterfly rounds; used at N = 2^15 and 2^16 only, 16
- * elsewhere). flags (8 words only): bit 0 accumulates the key products exactly
- * in 128 bits and reduces once per word; bit 1 exchanges the transform's words
- * between the rounds by warp shuffles instead of through shared memory.
+ * elsewhere). flags: bit 0 (8 words only) accumulates the key products exactly
+ * in 128 bits and reduces once per word; bit 1 (8 words only) exchanges the
+ * transform's words between the rounds by warp shuffles instead of through
+ * shared memory; bit 2 runs ModDown's last transform pass with 8 words per
+ * thread as well (N = 2^15, 2^16).
  * Default: 8 words, flags 1 (the fastest measured at N = 2^16). Speed only,
  * never results. PPST_E_ARG for other values. */
 int ppst_ctx_set_inner_shape(ppst_ctx *ctx, uint32_t words_per_thread, uint32_t flags);

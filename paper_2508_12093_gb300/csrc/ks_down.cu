@@ -164,6 +164,84 @@ __global__ void __launch_bounds__(PassShape<S, SUB>::THREADS, 2)
     }
 }
 
+// the same pass with 8 words per thread (N = 2^15, 2^16): one warp per 256-point
+// chunk, SUB chunks per block; z is read in natural order (words h + 32 k), the
+// tiles of acc and d and the output in the evaluation domain's storage order
+template <int SUB>
+struct Md8Smem {
+    static constexpr int TILE = SUB * 256;
+    static constexpr size_t A_OFF = 128;                           // acc tile
+    static constexpr size_t D_OFF = A_OFF + (size_t)TILE * 8;      // d tile
+    static constexpr size_t X_OFF = D_OFF + (size_t)TILE * 8;      // exchange buffers
+    static constexpr size_t BYTES = X_OFF + (size_t)TILE * 8;
+};
+
+template <bool RESC, int SUB>
+__global__ void __launch_bounds__(32 * SUB, SUB == 8 ? 3 : 6)
+    k_md_chunks8(const uint64_t *__restrict__ z, const uint64_t *__restrict__ acc, ItemPtrs ip,
+                 const MdC *__restrict__ mdc, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN,
+                 int nl, size_t ext_stride, size_t z_stride, size_t pstride, Ws ws, int *err)
+{
+    typedef Md8Smem<SUB> SM;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    const uint64_t *at = reinterpret_cast<const uint64_t *>(smem + SM::A_OFF);
+    const uint64_t *dt = reinterpret_cast<const uint64_t *>(smem + SM::D_OFF);
+    constexpr uint32_t TB = SM::TILE * 8;
+    const int N = 1 << logN;
+    const int it = blockIdx.y / (2 * nl), rem = blockIdx.y - it * 2 * nl;
+    const int k = rem / nl, i = rem - k * nl;
+    const PrimeC p = pc[i];
+    const MdC mc = mdc[i];
+    const size_t t0 = (size_t)i * N + (size_t)blockIdx.x * SM::TILE;  // the block's tile in a polynomial
+    const uint64_t *ad = (RESC || k == 0) ? ip.in0[it] + (size_t)k * pstride : nullptr;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_fence_init();
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar[0], ad ? 2 * TB : TB);
+        bulk_g2s(smem + SM::A_OFF, acc + it * ws.acc + (size_t)k * ext_stride + t0, TB, &bar[0]);
+        if (ad) bulk_g2s(smem + SM::D_OFF, ad + t0, TB, &bar[0]);
+    }
+    __syncthreads();
+    const int h = threadIdx.x & 31, sub = threadIdx.x >> 5;
+    const int g = blockIdx.x * SUB + sub;
+    uint64_t *ex = reinterpret_cast<uint64_t *>(smem + SM::X_OFF) + sub * 256;
+    uint64_t x[8];
+    const uint64_t *src = z + it * ws.conv + (size_t)k * z_stride + t0 + sub * 256 + h;
+#pragma unroll
+    for (int kk = 0; kk < 8; kk++) x[kk] = src[32 * kk];
+    const Tw *T = tw + (size_t)i * N;
+    chunks_fwd_core8<false>(x, ex, h, [&](int m, int j) { return ldtw(T + (size_t)m * ((N >> 8) + g) + j); },
+                            p.q);
+    if (__syncthreads_or(!mbar_wait(&bar[0], 0))) {  // the tiles did not arrive in time
+        if (threadIdx.x == 0) {
+            *(volatile int *)err = 1;
+            mbar_wait(&bar[0], 0);
+        }
+        return;
+    }
+    uint64_t *od = ip.out[it] + (size_t)k * pstride + t0;
+#pragma unroll
+    for (int kk = 0; kk < 8; kk++) {
+        const int a = sub * 256 + addr16(8 * h + kk);  // storage address of natural word 8 h + kk
+        const uint64_t Z = reduce4q(x[kk], p.q);
+        const uint64_t av = at[a];
+        uint64_t r;
+        if (RESC) {
+            const uint64_t dv = dt[a];
+            r = csub(shoup(dv, mc.qlinv.w, mc.qlinv.s, p.q), p.q);
+            r = add_mod(r, csub(shoup(av, mc.pq.w, mc.pq.s, p.q), p.q), p.q);
+            r = sub_mod(r, csub(shoup(Z, mc.qlinv.w, mc.qlinv.s, p.q), p.q), p.q);
+        } else {
+            r = csub(shoup(av, mc.pinv.w, mc.pinv.s, p.q), p.q);
+            if (ad) r = add_mod(r, dt[a], p.q);
+            r = sub_mod(r, Z, p.q);
+        }
+        od[a] = r;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // rescale after Mul(P) (Sec. 3.1 levels): out_i = c_i m_i q_l^-1 - NTT([c_l]_centred mod q_i) q_l^-1
 // ---------------------------------------------------------------------------
@@ -335,6 +413,24 @@ void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip)
         check_launch("k_md_cols");
     }
     ProfScope _ps(c, "moddown_chunks", (uint64_t)B * (RESC ? 8 : 7) * nl, (uint64_t)B * 2 * nl);  // writes out
+    if (ntt_s_chunk(c.logN) == 8 && c.md_words == 8) {  // 8 words per thread, tiles of 8 or 4 chunks
+        auto launch8 = [&](auto bv) {
+            constexpr int SUB = decltype(bv)::value;
+            const size_t smem = Md8Smem<SUB>::BYTES;
+            static std::atomic<bool> attr_set{false};
+            if (!attr_set.load()) {
+                PPST_CUDA(cudaFuncSetAttribute(k_md_chunks8<RESC, SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+                attr_set = true;
+            }
+            launch_on(c, k_md_chunks8<RESC, SUB>, dim3(c.N / Md8Smem<SUB>::TILE, B * 2 * nl), 32 * SUB, smem,
+                c.ws_conv, c.ws_acc, ip, mdc, c.d_pc, c.d_twf, c.logN, nl, es, ps, ps, ws, c.d_err);
+        };
+        if (pass_sub(c, 8, B * 2 * nl) >= 16) launch8(std::integral_constant<int, 8>{});
+        else launch8(std::integral_constant<int, 4>{});
+        check_launch("k_md_chunks8");
+        return;
+    }
     dispatch_pass(c, ntt_s_chunk(c.logN), B * 2 * nl, [&](auto sv, auto bv) {
         constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
         const size_t smem = MdSmem<S, SUB>::BYTES;
