@@ -283,8 +283,7 @@ struct Inner8Smem {
     static constexpr size_t X_OFF = 128;                              // two digit tiles
     static constexpr size_t K_OFF = X_OFF + 2 * (size_t)TILE * 8;    // two key tiles
     static constexpr size_t T_OFF = K_OFF + 2 * (size_t)TILE * 8;    // exchange buffers
-    static constexpr size_t W_OFF = T_OFF + (size_t)TILE * 8;        // the chunks' twiddles (255 each)
-    static constexpr size_t BYTES = W_OFF + (size_t)SUB * M * sizeof(Tw);
+    static constexpr size_t BYTES = T_OFF + (size_t)TILE * 8;
 };
 
 template <int SUB, bool LAZY, bool SHFL>
@@ -332,19 +331,9 @@ __global__ void __launch_bounds__(Inner8Smem<SUB>::THREADS, SUB == 8 ? 2 : 4)
     }
     __syncthreads();
     const int h = threadIdx.x & 31, sub = threadIdx.x >> 5;
+    const int g = tile * SUB + sub;
     uint64_t *ex = reinterpret_cast<uint64_t *>(smem + SM::T_OFF) + sub * SM::M;
-    // the 255 twiddles each chunk's pass uses (entry m + j: group j of the stage with
-    // m groups), loaded once and reused by every digit: entry i of chunk c is
-    // psi^brv of m (N / 256 + g_c) + (i - m), m the largest power of two <= i
-    Tw *twc = reinterpret_cast<Tw *>(smem + SM::W_OFF);
-    for (int i = threadIdx.x; i < SUB * SM::M; i += SM::THREADS) {
-        const int c = i >> 8, e = i & 255;
-        if (e == 0) continue;
-        const int m = 1 << (31 - __clz(e));
-        twc[i] = ldtw(T + (size_t)m * ((N >> 8) + tile * SUB + c) + (e - m));
-    }
-    __syncthreads();
-    const Tw *tc = twc + sub * SM::M;
+    const size_t tg = (size_t)(N >> 8) + g;  // twiddle of group j of a stage with m groups: T[m tg + j]
     int ka[8];  // tile offsets (storage order) of this thread's output words 8 h + k
 #pragma unroll
     for (int k = 0; k < 8; k++) ka[k] = sub * SM::M + addr16(8 * h + k);
@@ -366,7 +355,7 @@ __global__ void __launch_bounds__(Inner8Smem<SUB>::THREADS, SUB == 8 ? 2 : 4)
         } else {
 #pragma unroll
             for (int k = 0; k < 8; k++) x[k] = xt[sub * SM::M + h + 32 * k];
-            chunks_fwd_core8<SHFL>(x, ex, h, [&](int m, int jj) { return tc[m + jj]; }, p.q);
+            chunks_fwd_core8<SHFL>(x, ex, h, [&](int m, int jj) { return ldtw(T + m * tg + jj); }, p.q);
 #pragma unroll
             for (int k = 0; k < 8; k++) x[k] = reduce4q(x[k], p.q);
         }
