@@ -138,8 +138,9 @@ int ppst_ctx_set_pass_blocks(ppst_ctx *ctx, uint32_t min_blocks);
  * transform's words between the rounds by warp shuffles instead of through
  * shared memory; bit 2 runs ModDown's last transform pass with 8 words per
  * thread as well (N = 2^15, 2^16).
- * Default: 8 words, flags 1 (the fastest measured at N = 2^16). Speed only,
- * never results. PPST_E_ARG for other values. */
+ * Default: 8 words, flags 5 (lazy accumulation, 8-word ModDown: the fastest
+ * measured at N = 2^16). Speed only, never results. PPST_E_ARG for other
+ * values. */
 int ppst_ctx_set_inner_shape(ppst_ctx *ctx, uint32_t words_per_thread, uint32_t flags);
 /* Failure-detection self-test (no counterpart in the paper): launches one block
  * that waits on a shared-memory barrier nothing completes, bounded by timeout_us
