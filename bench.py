@@ -44,9 +44,12 @@ HMULT_BYTES = (2 * 2 * 24 + 6 * 2 * 28 + 2 * 24) * 65536 * 8
 # writes, intermediates included) from ncu captures of the current kernels; the
 # per-launch traffic reported is this ratio times the launch's fused bytes.
 # Filled in from the capture of the kernel as it now stands (empty: none yet).
-DRAM_PER_FUSED = {}
-DRAM_SOURCE = None
-# (filled from profiles/ once the final kernel has been captured)
+# k_inner8 (8 words per thread, lazy accumulation, tile 4) in a single-item top-level
+# HMult (python -m paper_2508_12093_gb300.profcase hmult): 293.75 MB read + 19.41 MB
+# written against 293.6 MB of fused bytes (560 limbs of 512 KiB)
+DRAM_PER_FUSED = {"inner_chunks": (293.752 + 19.410) / 293.601}
+DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_inner8 in a single-item top-level HMult "
+               "(313.16 MB against 293.60 MB of fused bytes: 1.067), times the step's fused bytes per launch")
 
 
 def peaks():
