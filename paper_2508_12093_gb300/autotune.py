@@ -33,11 +33,12 @@ if ROOT not in sys.path:
 CANDIDATES = (3, 4, 6, 12)
 TILES = (4, 8, 16)  # transform chunks per block of the key inner product
 # inner-product shapes: (words per thread, 128-bit lazy accumulation, warp-shuffle exchanges,
-# 8-word ModDown pass, tile)
-INNER = ((16, False, False, False, 4), (16, False, False, False, 8), (16, False, False, False, 16),
-         (8, False, False, False, 4), (8, False, False, False, 8), (8, True, False, False, 4),
-         (8, True, False, False, 8), (8, True, True, False, 4), (8, True, True, False, 8),
-         (8, True, False, True, 4), (8, True, False, True, 8))
+# 8-word ModDown pass, 8-word ModUp pass, tile)
+INNER = ((16, False, False, False, False, 4), (16, False, False, False, False, 8),
+         (16, False, False, False, False, 16), (8, False, False, False, False, 4),
+         (8, False, False, False, False, 8), (8, True, False, False, False, 4), (8, True, False, False, False, 8),
+         (8, True, True, False, False, 4), (8, True, True, False, False, 8), (8, True, False, True, False, 4),
+         (8, True, False, True, False, 8), (8, True, False, True, True, 4), (8, True, False, True, True, 8))
 PASS_BLOCKS = (0, 228, 456, 912)  # grid-size thresholds for smaller transform blocks
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuned.json")
 
@@ -78,19 +79,20 @@ def measure(params, reps=20, query=None, peak_gbs=None):
     sk, evk = ctx.keygen(2)  # relinearisation key and the Galois keys of rotations by 2^i
     a = ctx.encrypt_ints(evk, np.zeros(ctx.N, dtype=np.int64), 9, 0, 2.0 ** params["log_scale"])
     out = {"dnum": params["dnum"], "n_p": params["n_p"], "tile_us": {}, "inner_us": {}, "pass_blocks_us": {}}
-    for words, lazy, shfl, md8, tile in INNER:
+    for words, lazy, shfl, md8, mu8, tile in INNER:
         if words == 8 and params["log_n"] < 15:
             continue  # 8 words per thread exist for 256-point chunks only
-        ctx.set_inner_shape(words, lazy, shfl, md8)
+        ctx.set_inner_shape(words, lazy, shfl, md8, mu8)
         ctx.set_tile(tile)
         t = _timed(lambda: ctx.hmult(evk, a, a), reps)
-        out["inner_us"][f"{words}{'L' if lazy else ''}{'S' if shfl else ''}{'M' if md8 else ''}/{tile}"] = t
+        key = f"{words}{'L' if lazy else ''}{'S' if shfl else ''}{'M' if md8 else ''}{'U' if mu8 else ''}/{tile}"
+        out["inner_us"][key] = t
         if words == 16:
             out["tile_us"][str(tile)] = t
     best = min(out["inner_us"], key=out["inner_us"].get)
     w, tile = best.split("/")
-    out["inner"] = {"words": int(w.rstrip("LSM")), "lazy": "L" in w, "shuffle": "S" in w, "moddown8": "M" in w,
-                    "tile": int(tile)}
+    out["inner"] = {"words": int(w.rstrip("LSMU")), "lazy": "L" in w, "shuffle": "S" in w, "moddown8": "M" in w,
+                    "modup8": "U" in w, "tile": int(tile)}
     out["tile"] = int(tile)
     apply(ctx, out)
     out["hmult_us"] = out["inner_us"][best]
@@ -116,7 +118,8 @@ def measure(params, reps=20, query=None, peak_gbs=None):
 def apply(ctx, row):
     """Set a measured row's shapes (inner product, transform blocks) on a context."""
     inner = row.get("inner") or {"words": 16, "lazy": False, "tile": row.get("tile", 8)}
-    ctx.set_inner_shape(inner["words"], inner["lazy"], inner.get("shuffle", False), inner.get("moddown8", False))
+    ctx.set_inner_shape(inner["words"], inner["lazy"], inner.get("shuffle", False), inner.get("moddown8", False),
+                        inner.get("modup8", False))
     ctx.set_tile(inner["tile"])
     if "pass_min_blocks" in row:
         ctx.set_pass_blocks(row["pass_min_blocks"])

@@ -147,6 +147,41 @@ __global__ void __launch_bounds__(PassShape<S, SUB>::THREADS, 2)
     for (int k = 0; k < P::E; k++) out[(size_t)(P::E * h + k) * C + g] = x[k];
 }
 
+// the same pass with 8 words per thread (N = 2^15, 2^16: 256-row columns): SUB
+// columns per block, column `sub` on the 32 threads h; three butterfly rounds with
+// two block-wide exchanges through a swizzled shared-memory buffer
+template <int ALPHA, int SUB>
+__global__ void __launch_bounds__(32 * SUB, SUB == 8 ? 3 : 6)
+    k_modup_cols8(const uint64_t *__restrict__ y, uint64_t *__restrict__ ext, const uint64_t *__restrict__ ks,
+                  DigitOffs offs, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN, int level,
+                  int alpha, int L, int K, int nd, size_t ext_stride, Ws ws)
+{
+    __shared__ uint64_t sm[SUB * 256];
+    const int N = 1 << logN, C = N >> 8;
+    const int E_ext = level + 1 + K;
+    const int per_item = nd * E_ext;
+    const int it = blockIdx.y / per_item, rem = blockIdx.y - it * per_item;
+    const int j = rem / E_ext, e = rem - j * E_ext;
+    const int lo = j * alpha, hi = min(lo + alpha, level + 1), a = hi - lo;
+    if (e >= lo && e < hi) return;  // a digit's own limbs come from d itself (block-uniform)
+    const int t = e <= level ? e : L + 1 + (e - level - 1);
+    const PrimeC pt = pc[t];
+    __shared__ uint64_t f[16];
+    if (threadIdx.x < a) f[threadIdx.x] = ks[offs.off[j] + 2 * a + (size_t)threadIdx.x * E_ext + e];
+    __syncthreads();
+    const int sub = threadIdx.x % SUB, h = threadIdx.x / SUB;
+    const int g = blockIdx.x * SUB + sub;
+    uint64_t x[8];
+    const uint64_t *yl = y + it * ws.d2 + (size_t)lo * N + g;
+    if (ALPHA > 0 && a == ALPHA) bconv_words<ALPHA, 8, 32>(x, yl, f, a, N, C, h, pt);
+    else bconv_words<0, 8, 32>(x, yl, f, a, N, C, h, pt);  // a partial last digit
+    const Tw *T = tw + (size_t)t * N;
+    cols_fwd_core8<SUB>(x, sm, h, sub, [&](int m, int jj) { return ldtw(T + m + jj); }, pt.q);
+    uint64_t *out = ext + it * ws.ext + (size_t)j * ext_stride + (size_t)e * N;
+#pragma unroll
+    for (int k = 0; k < 8; k++) out[(size_t)(8 * h + k) * C + g] = x[k];
+}
+
 // ---------------------------------------------------------------------------
 // 3. CHUNKS pass fused with the key inner product
 // ---------------------------------------------------------------------------
@@ -441,6 +476,19 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
         uint64_t targets = 0;
         for (int j = 0; j < nd; j++) targets += E_ext - (std::min((j + 1) * c.alpha, level + 1) - j * c.alpha);
         ProfScope _ps(c, "modup_cols", (uint64_t)B * ((level + 1) + targets));  // limbs read once + written
+        if (ntt_s_rows(c.logN) == 8 && c.modup_words == 8) {  // 8 words per thread, 8 or 4 columns per block
+            dispatch_a(c.alpha, [&](auto av) {
+                constexpr int A = decltype(av)::value;
+                auto launch8 = [&](auto bv) {
+                    constexpr int SUB = decltype(bv)::value;
+                    launch_on(c, k_modup_cols8<A, SUB>, grid_s(c, 8, SUB, B * nd * E_ext), 32 * SUB, 0, c.ws_d2,
+                        c.ws_ext, c.d_ks, offs, c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, ws);
+                };
+                if (pass_sub(c, 8, (int)targets * B) >= 16) launch8(std::integral_constant<int, 8>{});
+                else launch8(std::integral_constant<int, 4>{});
+            });
+            check_launch("k_modup_cols8");
+        } else
         dispatch_pass(c, ntt_s_rows(c.logN), (int)targets * B, [&](auto sv, auto bv) {
             constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
             dispatch_a(c.alpha, [&](auto av) {

@@ -151,12 +151,12 @@ __device__ __forceinline__ void xchg_bc_shfl(uint64_t (&x)[8], int h)
     for (int k = 0; k < 8; k++) x[k] = y[k];
 }
 
-// forward CHUNKS pass of a chunk, 8 words per thread: words h + 32 k in, 8 h + k out;
-// the exchanges go through the warp's shared-memory buffer `ex` or (SHFL) through
-// shuffles. tw(m, j) is the twiddle of group j of the stage with m groups per chunk
-// (distance 128 / m): psi^brv of m (N / 256 + g) + j for chunk g.
-template <bool SHFL, class TwF>
-__device__ __forceinline__ void chunks_fwd_core8(uint64_t (&x)[8], uint64_t *ex, int h, TwF &&tw, uint64_t q)
+// the three butterfly rounds of a 256-point forward pass with 8 words per thread:
+// words h + 32 k in, 8 h + k out. tw(m, j) is the twiddle of group j of the
+// stage with m groups (distance 128 / m); xab / xbc move the words from layout
+// A (h + 32 k) to B (32 (h >> 2) + 4 k + (h & 3)) and from B to C (8 h + k).
+template <class TwF, class XAB, class XBC>
+__device__ __forceinline__ void fwd_rounds8(uint64_t (&x)[8], int h, TwF &&tw, XAB &&xab, XBC &&xbc, uint64_t q)
 {
     const uint64_t q2 = 2 * q;
 #pragma unroll
@@ -167,17 +167,8 @@ __device__ __forceinline__ void chunks_fwd_core8(uint64_t (&x)[8], uint64_t *ex,
             bfly_fwd(x[k], x[k + (1 << s)], tw(4 >> s, k >> (s + 1)), q, q2);
         }
     }
-    const int hh = h >> 2, hl = h & 3;
-    if (SHFL) {
-        xchg_ab_shfl(x, h);
-    } else {
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < 8; k++) ex[swz8(h + 32 * k)] = x[k];
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < 8; k++) x[k] = ex[swz8(32 * hh + 4 * k + hl)];
-    }
+    xab(x);
+    const int hh = h >> 2;
 #pragma unroll
     for (int s = 2; s >= 0; s--) {  // distance 4 << s: m = 32 >> s, group (hh << (2 - s)) | (k >> (s + 1))
 #pragma unroll
@@ -186,16 +177,7 @@ __device__ __forceinline__ void chunks_fwd_core8(uint64_t (&x)[8], uint64_t *ex,
             bfly_fwd(x[k], x[k + (1 << s)], tw(32 >> s, (hh << (2 - s)) | (k >> (s + 1))), q, q2);
         }
     }
-    if (SHFL) {
-        xchg_bc_shfl(x, h);
-    } else {
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < 8; k++) ex[swz8(32 * hh + 4 * k + hl)] = x[k];
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < 8; k++) x[k] = ex[swz8(8 * h + k)];
-    }
+    xbc(x);
 #pragma unroll
     for (int s = 1; s >= 0; s--) {  // distance 1 << s: m = 128 >> s, group (8 h + k) >> (s + 1)
 #pragma unroll
@@ -204,6 +186,73 @@ __device__ __forceinline__ void chunks_fwd_core8(uint64_t (&x)[8], uint64_t *ex,
             bfly_fwd(x[k], x[k + (1 << s)], tw(128 >> s, (8 * h + k) >> (s + 1)), q, q2);
         }
     }
+}
+
+// forward CHUNKS pass of a chunk (one warp), 8 words per thread; the exchanges go
+// through the warp's shared-memory buffer `ex` or (SHFL) through shuffles; tw(m, j)
+// is psi^brv of m (N / 256 + g) + j for chunk g
+template <bool SHFL, class TwF>
+__device__ __forceinline__ void chunks_fwd_core8(uint64_t (&x)[8], uint64_t *ex, int h, TwF &&tw, uint64_t q)
+{
+    const int hh = h >> 2, hl = h & 3;
+    auto xab = [&](uint64_t(&v)[8]) {
+        if (SHFL) {
+            xchg_ab_shfl(v, h);
+            return;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) ex[swz8(h + 32 * k)] = v[k];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = ex[swz8(32 * hh + 4 * k + hl)];
+    };
+    auto xbc = [&](uint64_t(&v)[8]) {
+        if (SHFL) {
+            xchg_bc_shfl(v, h);
+            return;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) ex[swz8(32 * hh + 4 * k + hl)] = v[k];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = ex[swz8(8 * h + k)];
+    };
+    fwd_rounds8(x, h, tw, xab, xbc, q);
+}
+
+// forward COLS pass, 8 words per thread: SUB columns per block, column `sub` held by
+// the 32 threads h; row p of column sub sits at (p SUB + sub) ^ (((p >> 3) & (16 / SUB - 1)) SUB)
+// in the block's buffer (conflict-free for the three layouts, checked exhaustively);
+// tw(m, j) is psi^brv of m + j (the first stages of the transform)
+template <int SUB>
+__device__ __forceinline__ int cols8_smem(int p, int sub)
+{
+    return (p * SUB + sub) ^ (((p >> 3) & (16 / SUB - 1)) * SUB);
+}
+
+template <int SUB, class TwF>
+__device__ __forceinline__ void cols_fwd_core8(uint64_t (&x)[8], uint64_t *sm, int h, int sub, TwF &&tw, uint64_t q)
+{
+    const int hh = h >> 2, hl = h & 3;
+    auto xab = [&](uint64_t(&v)[8]) {
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 8; k++) sm[cols8_smem<SUB>(h + 32 * k, sub)] = v[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = sm[cols8_smem<SUB>(32 * hh + 4 * k + hl, sub)];
+    };
+    auto xbc = [&](uint64_t(&v)[8]) {
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 8; k++) sm[cols8_smem<SUB>(32 * hh + 4 * k + hl, sub)] = v[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = sm[cols8_smem<SUB>(8 * h + k, sub)];
+    };
+    fwd_rounds8(x, h, tw, xab, xbc, q);
 }
 
 // ModDown (+ rescale) of the accumulators of B items (ks_down.cu)

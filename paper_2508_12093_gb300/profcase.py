@@ -19,8 +19,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-SHAPES = {"e16": (16, False, False, False), "e8": (8, False, False, False), "e8lazy": (8, True, False, False),
-          "e8lazyshfl": (8, True, True, False), "e8lazymd8": (8, True, False, True)}
+SHAPES = {"e16": (16, False, False, False, False), "e8": (8, False, False, False, False),
+          "e8lazy": (8, True, False, False, False), "e8lazyshfl": (8, True, True, False, False),
+          "e8lazymd8": (8, True, False, True, False), "e8all": (8, True, False, True, True)}
 
 
 def stages(specs=("6",), reps=20):
