@@ -457,11 +457,13 @@ class Context:
         self.inner_sub = int(inner_sub)
 
 
-    def set_inner_shape(self, words_per_thread, lazy=False, shuffle=False, moddown8=False, modup8=False):
+    def set_inner_shape(self, words_per_thread, lazy=False, shuffle=False, moddown8=False, modup8=False,
+                        inverse8=False):
         """ppst_ctx_set_inner_shape: 16 or 8 words per thread in the inner product, lazy 128-bit
-        accumulation and warp-shuffle exchanges (8 words only), 8-word ModDown and ModUp passes;
-        speed only."""
-        flags = int(bool(lazy)) | (2 if shuffle else 0) | (4 if moddown8 else 0) | (8 if modup8 else 0)
+        accumulation and warp-shuffle exchanges (8 words only), 8-word ModDown CHUNKS pass, COLS
+        passes and first inverse passes; speed only."""
+        flags = (int(bool(lazy)) | (2 if shuffle else 0) | (4 if moddown8 else 0) | (8 if modup8 else 0)
+                 | (16 if inverse8 else 0))
         self._check(lib.ppst_ctx_set_inner_shape(self.ptr, int(words_per_thread), flags))
 
     def set_pass_blocks(self, min_blocks):

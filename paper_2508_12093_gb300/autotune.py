@@ -32,13 +32,21 @@ if ROOT not in sys.path:
 
 CANDIDATES = (3, 4, 6, 12)
 TILES = (4, 8, 16)  # transform chunks per block of the key inner product
-# inner-product shapes: (words per thread, 128-bit lazy accumulation, warp-shuffle exchanges,
-# 8-word ModDown pass, 8-word ModUp pass, tile)
-INNER = ((16, False, False, False, False, 4), (16, False, False, False, False, 8),
-         (16, False, False, False, False, 16), (8, False, False, False, False, 4),
-         (8, False, False, False, False, 8), (8, True, False, False, False, 4), (8, True, False, False, False, 8),
-         (8, True, True, False, False, 4), (8, True, True, False, False, 8), (8, True, False, True, False, 4),
-         (8, True, False, True, False, 8), (8, True, False, True, True, 4), (8, True, False, True, True, 8))
+# kernel shapes: words per thread of the inner product, 128-bit lazy accumulation,
+# warp-shuffle exchanges, 8-word ModDown CHUNKS pass, 8-word COLS passes, 8-word first
+# inverse passes, inner-product tile (chunks per block)
+FLAGS = ("lazy", "shuffle", "moddown8", "modup8", "inverse8")
+INNER = [dict(words=16, tile=4), dict(words=16, tile=8), dict(words=16, tile=16),
+         dict(words=8, tile=4), dict(words=8, tile=8), dict(words=8, lazy=True, tile=4),
+         dict(words=8, lazy=True, tile=8), dict(words=8, lazy=True, shuffle=True, tile=4),
+         dict(words=8, lazy=True, moddown8=True, tile=4), dict(words=8, lazy=True, moddown8=True, tile=8),
+         dict(words=8, lazy=True, moddown8=True, modup8=True, tile=4),
+         dict(words=8, lazy=True, moddown8=True, inverse8=True, tile=4),
+         dict(words=8, lazy=True, moddown8=True, modup8=True, inverse8=True, tile=4)]
+
+
+def shape_name(sh):
+    return f"{sh['words']}" + "".join("+" + f for f in FLAGS if sh.get(f)) + f"/{sh['tile']}"
 PASS_BLOCKS = (0, 228, 456, 912)  # grid-size thresholds for smaller transform blocks
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuned.json")
 
@@ -79,23 +87,21 @@ def measure(params, reps=20, query=None, peak_gbs=None):
     sk, evk = ctx.keygen(2)  # relinearisation key and the Galois keys of rotations by 2^i
     a = ctx.encrypt_ints(evk, np.zeros(ctx.N, dtype=np.int64), 9, 0, 2.0 ** params["log_scale"])
     out = {"dnum": params["dnum"], "n_p": params["n_p"], "tile_us": {}, "inner_us": {}, "pass_blocks_us": {}}
-    for words, lazy, shfl, md8, mu8, tile in INNER:
-        if words == 8 and params["log_n"] < 15:
-            continue  # 8 words per thread exist for 256-point chunks only
-        ctx.set_inner_shape(words, lazy, shfl, md8, mu8)
-        ctx.set_tile(tile)
+    shapes = {}
+    for sh in INNER:
+        if params["log_n"] < 15 and (sh["words"] == 8 or any(sh.get(f) for f in FLAGS)):
+            continue  # the 8-word forms exist for 256-point chunks (N = 2^15, 2^16) only
+        apply(ctx, {"inner": sh})
         t = _timed(lambda: ctx.hmult(evk, a, a), reps)
-        key = f"{words}{'L' if lazy else ''}{'S' if shfl else ''}{'M' if md8 else ''}{'U' if mu8 else ''}/{tile}"
-        out["inner_us"][key] = t
-        if words == 16:
-            out["tile_us"][str(tile)] = t
+        out["inner_us"][shape_name(sh)] = t
+        shapes[shape_name(sh)] = sh
+        if sh["words"] == 16 and not any(sh.get(f) for f in FLAGS):
+            out["tile_us"][str(sh["tile"])] = t
     best = min(out["inner_us"], key=out["inner_us"].get)
-    w, tile = best.split("/")
-    out["inner"] = {"words": int(w.rstrip("LSMU")), "lazy": "L" in w, "shuffle": "S" in w, "moddown8": "M" in w,
-                    "modup8": "U" in w, "tile": int(tile)}
-    out["tile"] = int(tile)
+    out["inner"] = dict({f: False for f in FLAGS}, **shapes[best])
+    out["tile"] = out["inner"]["tile"]
     apply(ctx, out)
-    out["hmult_us"] = out["inner_us"][best]
+    out["hmult_us"] = out["inner_us"][best]  # the best shape's top-level HMult
     low = ctx.drop(a, min(4, params["n_q"] - 1))
     for mb in PASS_BLOCKS:
         ctx.set_pass_blocks(mb)
@@ -117,9 +123,8 @@ def measure(params, reps=20, query=None, peak_gbs=None):
 
 def apply(ctx, row):
     """Set a measured row's shapes (inner product, transform blocks) on a context."""
-    inner = row.get("inner") or {"words": 16, "lazy": False, "tile": row.get("tile", 8)}
-    ctx.set_inner_shape(inner["words"], inner["lazy"], inner.get("shuffle", False), inner.get("moddown8", False),
-                        inner.get("modup8", False))
+    inner = row.get("inner") or {"words": 16, "tile": row.get("tile", 8)}
+    ctx.set_inner_shape(inner["words"], **{f: bool(inner.get(f, False)) for f in FLAGS})
     ctx.set_tile(inner["tile"])
     if "pass_min_blocks" in row:
         ctx.set_pass_blocks(row["pass_min_blocks"])

@@ -109,12 +109,13 @@ int ppst_ctx_set_inner_shape(ppst_ctx *ctx, uint32_t words_per_thread, uint32_t 
     if (!ok(c, TAG_CTX)) return PPST_E_ARG;
     return guard(c, [&] {
         REQ(words_per_thread == 8 || words_per_thread == 16, "words_per_thread must be 8 or 16");
-        REQ(flags <= 15 && ((flags & 3) == 0 || words_per_thread == 8), "flags 1, 2 need 8 words per thread");
+        REQ(flags <= 31 && ((flags & 3) == 0 || words_per_thread == 8), "flags 1, 2 need 8 words per thread");
         c->inner_words = (int)words_per_thread;
         c->inner_lazy = (flags & 1) != 0;
         c->inner_shfl = (flags & 2) != 0;
         c->md_words = (flags & 4) ? 8 : 16;
         c->modup_words = (flags & 8) ? 8 : 16;
+        c->inv_words = (flags & 16) ? 8 : 16;
     });
 }
 

@@ -76,6 +76,44 @@ __global__ void __launch_bounds__(PassShape<S, SUB>::THREADS, PassShape<S, SUB>:
     for (int k = 0; k < P::E; k++) o[P::T * k] = x[k];
 }
 
+// the tensor product with 8 words per thread (256-point chunks: N = 2^15, 2^16), one
+// warp per chunk: the products at the storage addresses of natural words 8 h + k,
+// then the first inverse pass of d2, which leaves in natural order (words h + 32 k)
+template <int SUB>
+__global__ void __launch_bounds__(32 * SUB, SUB == 8 ? 4 : 8)
+    k_tensor_ic8(ItemPtrs ip, uint64_t *__restrict__ d2, uint64_t *__restrict__ d2n, const PrimeC *__restrict__ pc,
+                 const Tw *__restrict__ twi, int logN, int nl, size_t pstride, size_t d2_stride)
+{
+    __shared__ uint64_t ex_all[SUB * 256];
+    const int N = 1 << logN;
+    const int it = blockIdx.y / nl, i = blockIdx.y - it * nl;
+    const PrimeC p = pc[i];
+    const int h = threadIdx.x & 31, sub = threadIdx.x >> 5;
+    const int g = blockIdx.x * SUB + sub;
+    const size_t base = (size_t)i * N + (size_t)g * 256;
+    const uint64_t *a = ip.in0[it], *b = ip.in1[it];
+    uint64_t *t = ip.out[it];
+    uint64_t x[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const size_t off = base + addr16(8 * h + k);
+        const uint64_t x0 = a[off], x1 = a[pstride + off], y0 = b[off], y1 = b[pstride + off];
+        t[off] = mul_mod(x0, y0, p);
+        x[k] = mul_mod(x1, y1, p);
+        d2n[it * d2_stride + off] = x[k];
+        Acc128 acc{0, 0};
+        mac(acc, x0, y1);
+        mac(acc, x1, y0);
+        t[pstride + off] = mont_mul(mont_redc(acc.hi, acc.lo, p.q, p.qinv), p.r2, p.q, p.qinv);
+    }
+    const Tw *T = twi + (size_t)i * N;
+    const size_t tg = (size_t)(N >> 8) + g;
+    chunks_inv_core8(x, ex_all + sub * 256, h, [&](int m, int j) { return ldtw(T + m * tg + j); }, p.q);
+    uint64_t *o = d2 + it * d2_stride + base;
+#pragma unroll
+    for (int k = 0; k < 8; k++) o[h + 32 * k] = x[k];
+}
+
 // blockIdx.y = (item, poly, limb): poly 0 -> out[item].c0, poly 1 -> d2n and (after the pass) d2
 template <int S, int SUB>
 __global__ void __launch_bounds__(PassShape<S, SUB>::THREADS, PassShape<S, SUB>::MIN_BLOCKS)
@@ -587,6 +625,15 @@ std::vector<CtObj *> ev_hmult_batch(Ctx &c, const EvkObj &k, const std::vector<c
         }
         {
             ProfScope _ps(c, "tensor", (uint64_t)B * 7 * (lv + 1), (uint64_t)B * 4 * (lv + 1));  // reads a, b
+            if (ntt_s_chunk(c.logN) == 8 && c.inv_words == 8) {  // 8 words per thread
+                auto launch8 = [&](auto bv) {
+                    constexpr int SUB = decltype(bv)::value;
+                    launch_on(c, k_tensor_ic8<SUB>, dim3(c.N / (256 * SUB), B * (lv + 1)), 32 * SUB, 0, ip, c.ws_d2,
+                        c.ws_d2n, c.d_pc, c.d_twi, c.logN, lv + 1, ps, ws.d2);
+                };
+                if (pass_sub(c, 8, B * (lv + 1)) >= 16) launch8(std::integral_constant<int, 8>{});
+                else launch8(std::integral_constant<int, 4>{});
+            } else
             dispatch_pass(c, ntt_s_chunk(c.logN), B * (lv + 1), [&](auto sv, auto bv) {
                 constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
                 launch_on(c, k_tensor_ic<S, SUB>, grid_s(c, S, SUB, B * (lv + 1)), PassShape<S, SUB>::THREADS, 0,

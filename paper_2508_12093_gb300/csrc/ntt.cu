@@ -83,6 +83,31 @@ __global__ void __launch_bounds__(PassShape<S, SUB>::THREADS, PassShape<S, SUB>:
     for (int k = 0; k < P::E; k++) a[h + P::T * k] = x[k];
 }
 
+// the first inverse pass with 8 words per thread (256-point chunks: N = 2^15, 2^16),
+// one warp per chunk, SUB chunks per block: reads the evaluation domain's storage
+// order, writes natural order (in place: a warp reads its whole chunk before any
+// of its lanes writes)
+template <int SUB>
+__global__ void __launch_bounds__(32 * SUB, SUB == 8 ? 4 : 8)
+    k_ntt_inv_chunks8(LimbMap map, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN)
+{
+    __shared__ uint64_t ex_all[SUB * 256];
+    const int N = 1 << logN;
+    const int b = blockIdx.y, p = map.prime(b);
+    const uint64_t q = pc[p].q;
+    const int h = threadIdx.x & 31, sub = threadIdx.x >> 5;
+    const int g = blockIdx.x * SUB + sub;
+    uint64_t *a = map.ptr(b, N) + (size_t)g * 256;
+    uint64_t x[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = a[addr16(8 * h + k)];
+    const Tw *T = tw + (size_t)p * N;
+    const size_t tg = (size_t)(N >> 8) + g;
+    chunks_inv_core8(x, ex_all + sub * 256, h, [&](int m, int j) { return ldtw(T + m * tg + j); }, q);
+#pragma unroll
+    for (int k = 0; k < 8; k++) a[h + 32 * k] = x[k];
+}
+
 // last inverse pass; the result is multiplied by N^-1, or by outmul[i] for limb
 // i of its polynomial (N^-1 times a constant of the caller's), and reduced to [0, q)
 template <int S, int SUB>
@@ -149,6 +174,18 @@ void ntt_inv_mul(Ctx &c, const LimbMap &m, const Tw *outmul)
     if (m.count() == 0) return;
     {
         ProfScope _ps(c, "ntt_chunks_inv", (uint64_t)2 * m.count());
+        if (ntt_s_chunk(c.logN) == 8 && c.inv_words == 8) {  // 8 words per thread, 8 or 4 chunks per block
+            auto launch8 = [&](auto bv) {
+                constexpr int SUB = decltype(bv)::value;
+                launch_on(c, k_ntt_inv_chunks8<SUB>, dim3(c.N / (256 * SUB), m.count()), 32 * SUB, 0, m, c.d_pc,
+                    c.d_twi, c.logN);
+            };
+            if (pass_sub(c, 8, m.count()) >= 16) launch8(std::integral_constant<int, 8>{});
+            else launch8(std::integral_constant<int, 4>{});
+            check_launch("ntt_chunks_inv8");
+            ntt_inv_cols_mul(c, m, outmul);
+            return;
+        }
         dispatch_pass(c, ntt_s_chunk(c.logN), m, [&](auto sv, auto bv) {
             constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
             launch_on(c, k_ntt_inv_chunks<S, SUB>, pass_grid<S, SUB>(c, m), PassShape<S, SUB>::THREADS, 0, m,

@@ -266,6 +266,233 @@ __device__ __forceinline__ void cols_inv_core(uint64_t (&x)[PassShape<S>::E], ui
     }
 }
 
+// ---------------------------------------------------------------------------
+// 256-point passes with 8 words per thread (N = 2^15, 2^16): CHUNKS passes with one
+// warp per chunk (the inner product, ModDown, the inverse transforms), COLS passes
+// with SUB columns per block (ModUp, ModDown)
+// ---------------------------------------------------------------------------
+// XOR swizzle of a chunk's 256 words: the three layouts a warp uses (h + 32 k,
+// 32 (h >> 2) + 4 k + (h & 3), 8 h + k) each touch 16 distinct 8-byte banks
+// per half-warp
+__device__ __forceinline__ int swz8(int p) { return p ^ ((p >> 4) & 7) ^ (((p >> 5) & 1) << 3); }
+
+// where natural word p of a 256-word chunk is stored in the evaluation domain
+// (the 16-word storage order of ntt.cuh: E h + k -> h + 16 k)
+__device__ __forceinline__ int addr16(int p) { return (p >> 4) + ((p & 15) << 4); }
+
+// The two exchanges by warp shuffles instead of shared memory (a variant the
+// autotuner measures). A -> B swaps lane bits 2..4 with register bits 0..2
+// (three butterfly-pattern rounds of shfl.xor 4, 8, 16); B -> C transposes, for
+// each register parity, lane bits 0..1 with register bits 1..2 (rounds 1, 2).
+// Each round sends the half of the registers the partner needs and keeps the rest.
+__device__ __forceinline__ void xchg_ab_shfl(uint64_t (&x)[8], int h)
+{
+#pragma unroll
+    for (int bit = 0; bit < 3; bit++) {
+        const int s = 4 << bit, sv = 1 << bit;
+        const bool up = h & s;
+#pragma unroll
+        for (int a = 0; a < 8; a++) {
+            if (a & sv) continue;
+            const uint64_t send = up ? x[a] : x[a | sv];
+            const uint64_t recv = __shfl_xor_sync(0xffffffffu, send, s);
+            if (up) x[a] = recv;
+            else x[a | sv] = recv;
+        }
+    }
+}
+
+__device__ __forceinline__ void xchg_bc_shfl(uint64_t (&x)[8], int h)
+{
+    uint64_t y[8];
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+        uint64_t m[4] = {x[b], x[2 + b], x[4 + b], x[6 + b]};
+#pragma unroll
+        for (int s = 1; s <= 2; s <<= 1) {
+            const bool up = h & s;
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                if (a & s) continue;
+                const uint64_t send = up ? m[a] : m[a | s];
+                const uint64_t recv = __shfl_xor_sync(0xffffffffu, send, s);
+                if (up) m[a] = recv;
+                else m[a | s] = recv;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++) y[r + 4 * b] = m[r];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = y[k];
+}
+
+// the three butterfly rounds of a 256-point forward pass with 8 words per thread:
+// words h + 32 k in, 8 h + k out. tw(m, j) is the twiddle of group j of the
+// stage with m groups (distance 128 / m); xab / xbc move the words from layout
+// A (h + 32 k) to B (32 (h >> 2) + 4 k + (h & 3)) and from B to C (8 h + k).
+template <class TwF, class XAB, class XBC>
+__device__ __forceinline__ void fwd_rounds8(uint64_t (&x)[8], int h, TwF &&tw, XAB &&xab, XBC &&xbc, uint64_t q)
+{
+    const uint64_t q2 = 2 * q;
+#pragma unroll
+    for (int s = 2; s >= 0; s--) {  // distance 32 << s: m = 4 >> s groups, group k >> (s + 1)
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if ((k >> s) & 1) continue;
+            bfly_fwd(x[k], x[k + (1 << s)], tw(4 >> s, k >> (s + 1)), q, q2);
+        }
+    }
+    xab(x);
+    const int hh = h >> 2;
+#pragma unroll
+    for (int s = 2; s >= 0; s--) {  // distance 4 << s: m = 32 >> s, group (hh << (2 - s)) | (k >> (s + 1))
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if ((k >> s) & 1) continue;
+            bfly_fwd(x[k], x[k + (1 << s)], tw(32 >> s, (hh << (2 - s)) | (k >> (s + 1))), q, q2);
+        }
+    }
+    xbc(x);
+#pragma unroll
+    for (int s = 1; s >= 0; s--) {  // distance 1 << s: m = 128 >> s, group (8 h + k) >> (s + 1)
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if ((k >> s) & 1) continue;
+            bfly_fwd(x[k], x[k + (1 << s)], tw(128 >> s, (8 * h + k) >> (s + 1)), q, q2);
+        }
+    }
+}
+
+// forward CHUNKS pass of a chunk (one warp), 8 words per thread; the exchanges go
+// through the warp's shared-memory buffer `ex` or (SHFL) through shuffles; tw(m, j)
+// is psi^brv of m (N / 256 + g) + j for chunk g
+template <bool SHFL, class TwF>
+__device__ __forceinline__ void chunks_fwd_core8(uint64_t (&x)[8], uint64_t *ex, int h, TwF &&tw, uint64_t q)
+{
+    const int hh = h >> 2, hl = h & 3;
+    auto xab = [&](uint64_t(&v)[8]) {
+        if (SHFL) {
+            xchg_ab_shfl(v, h);
+            return;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) ex[swz8(h + 32 * k)] = v[k];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = ex[swz8(32 * hh + 4 * k + hl)];
+    };
+    auto xbc = [&](uint64_t(&v)[8]) {
+        if (SHFL) {
+            xchg_bc_shfl(v, h);
+            return;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) ex[swz8(32 * hh + 4 * k + hl)] = v[k];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = ex[swz8(8 * h + k)];
+    };
+    fwd_rounds8(x, h, tw, xab, xbc, q);
+}
+
+// the three butterfly rounds of a 256-point inverse (Gentleman-Sande) pass with 8
+// words per thread: words 8 h + k in (layout C), h + 32 k out (layout A), distances
+// 1, 2 | 4, 8, 16 | 32, 64, 128; xcb / xba move the words from C to B and from B
+// to A; tw(m, j) as for the forward rounds (inverse twiddles)
+template <class TwF, class XCB, class XBA>
+__device__ __forceinline__ void inv_rounds8(uint64_t (&x)[8], int h, TwF &&tw, XCB &&xcb, XBA &&xba, uint64_t q)
+{
+    const uint64_t q2 = 2 * q;
+#pragma unroll
+    for (int s = 0; s <= 1; s++) {  // distance 1 << s: m = 128 >> s, group (8 h + k) >> (s + 1)
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if ((k >> s) & 1) continue;
+            bfly_inv(x[k], x[k + (1 << s)], tw(128 >> s, (8 * h + k) >> (s + 1)), q, q2);
+        }
+    }
+    xcb(x);
+    const int hh = h >> 2;
+#pragma unroll
+    for (int s = 0; s <= 2; s++) {  // distance 4 << s: m = 32 >> s, group (hh << (2 - s)) | (k >> (s + 1))
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if ((k >> s) & 1) continue;
+            bfly_inv(x[k], x[k + (1 << s)], tw(32 >> s, (hh << (2 - s)) | (k >> (s + 1))), q, q2);
+        }
+    }
+    xba(x);
+#pragma unroll
+    for (int s = 0; s <= 2; s++) {  // distance 32 << s: m = 4 >> s, group k >> (s + 1)
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if ((k >> s) & 1) continue;
+            bfly_inv(x[k], x[k + (1 << s)], tw(4 >> s, k >> (s + 1)), q, q2);
+        }
+    }
+}
+
+// inverse CHUNKS pass of a chunk (one warp), 8 words per thread, exchanges through the
+// warp's swizzled shared-memory buffer; tw(m, j) is psi^-brv of m (N / 256 + g) + j
+template <class TwF>
+__device__ __forceinline__ void chunks_inv_core8(uint64_t (&x)[8], uint64_t *ex, int h, TwF &&tw, uint64_t q)
+{
+    const int hh = h >> 2, hl = h & 3;
+    auto xcb = [&](uint64_t(&v)[8]) {
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) ex[swz8(8 * h + k)] = v[k];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = ex[swz8(32 * hh + 4 * k + hl)];
+    };
+    auto xba = [&](uint64_t(&v)[8]) {
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) ex[swz8(32 * hh + 4 * k + hl)] = v[k];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = ex[swz8(h + 32 * k)];
+    };
+    inv_rounds8(x, h, tw, xcb, xba, q);
+}
+
+// forward COLS pass, 8 words per thread: SUB columns per block, column `sub` held by
+// the 32 threads h; row p of column sub sits at (p SUB + sub) ^ (((p >> 3) & (16 / SUB - 1)) SUB)
+// in the block's buffer (conflict-free for the three layouts, checked exhaustively);
+// tw(m, j) is psi^brv of m + j (the first stages of the transform)
+template <int SUB>
+__device__ __forceinline__ int cols8_smem(int p, int sub)
+{
+    return (p * SUB + sub) ^ (((p >> 3) & (16 / SUB - 1)) * SUB);
+}
+
+template <int SUB, class TwF>
+__device__ __forceinline__ void cols_fwd_core8(uint64_t (&x)[8], uint64_t *sm, int h, int sub, TwF &&tw, uint64_t q)
+{
+    const int hh = h >> 2, hl = h & 3;
+    auto xab = [&](uint64_t(&v)[8]) {
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 8; k++) sm[cols8_smem<SUB>(h + 32 * k, sub)] = v[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = sm[cols8_smem<SUB>(32 * hh + 4 * k + hl, sub)];
+    };
+    auto xbc = [&](uint64_t(&v)[8]) {
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 8; k++) sm[cols8_smem<SUB>(32 * hh + 4 * k + hl, sub)] = v[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = sm[cols8_smem<SUB>(8 * h + k, sub)];
+    };
+    fwd_rounds8(x, h, tw, xab, xbc, q);
+}
+
 // calls f(std::integral_constant<int, sub>) for the sub-transforms per block of
 // a pass of size 2^S: 16, 8 or 4 at S = 8 (N = 2^15, 2^16), 16 or 4 below
 // (where 8 is rounded down to 4: fewer kernels to compile)

@@ -19,17 +19,19 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-SHAPES = {"e16": (16, False, False, False, False), "e8": (8, False, False, False, False),
-          "e8lazy": (8, True, False, False, False), "e8lazyshfl": (8, True, True, False, False),
-          "e8lazymd8": (8, True, False, True, False), "e8all": (8, True, False, True, True)}
+SHAPES = {"e16": (16, False, False, False, False, False), "e8": (8, False, False, False, False, False),
+          "e8lazy": (8, True, False, False, False, False), "e8lazyshfl": (8, True, True, False, False, False),
+          "e8lazymd8": (8, True, False, True, False, False), "e8cols": (8, True, False, True, True, False),
+          "e8inv": (8, True, False, True, False, True), "e8all": (8, True, False, True, True, True)}
 
 
 def stages(specs=("6",), reps=20):
     """Per-kernel-class GPU time (CUDA events on the library's stream, mean of
     `reps` launches) of HMult and rotation at levels 23, 12 and 4, and the
     whole op's median time, for each spec "dnum" or "dnum:shape" (shape: e16,
-    e8, e8lazy, e8lazyshfl, e8lazymd8: the inner product's words per thread, lazy
-    accumulation, shuffle exchanges, 8-word ModDown pass); one JSON line each."""
+    e8, e8lazy, e8lazyshfl, e8lazymd8, e8cols, e8inv, e8all: the inner product's words
+    per thread, lazy accumulation, shuffle exchanges, 8-word ModDown CHUNKS pass, COLS
+    passes, first inverse passes); one JSON line each."""
     import json
     import torch
     import paper_2508_12093_gb300 as pp

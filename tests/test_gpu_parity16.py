@@ -48,21 +48,22 @@ def test_every_dnum_full_size(dnum):
         al = ctx.drop(a, lv)
         check(ctx, ctx.hmult(evk, al, b), want[("hmult", lv)], f"dnum {dnum} hmult level {lv}")
         check(ctx, ctx.rotate(evk, al, oj.ROT), want[("rot", lv)], f"dnum {dnum} rotation level {lv}")
-    # every inner-product shape (words per thread, lazy accumulation, tile) at the top level
-    for words, lazy, shfl, md8, mu8, tile in ((16, False, False, False, False, 4),
-                                              (16, False, False, False, False, 8),
-                                              (16, False, False, False, False, 16), (8, False, False, False, False, 4),
-                                              (8, False, False, False, False, 8), (8, True, False, False, False, 4),
-                                              (8, True, False, False, False, 8), (8, True, True, False, False, 4),
-                                              (8, False, True, False, False, 8), (8, True, False, True, False, 4),
-                                              (16, False, False, True, False, 8), (8, True, False, True, True, 4),
-                                              (16, False, False, False, True, 8)):
-        ctx.set_inner_shape(words, lazy, shfl, md8, mu8)
+    # every kernel shape at the top level (words per thread of the inner product, lazy
+    # accumulation, shuffle exchanges, 8-word ModDown / COLS / first inverse passes, tile)
+    shapes = [dict(words=16, tile=4), dict(words=16, tile=8), dict(words=16, tile=16), dict(words=8, tile=4),
+              dict(words=8, tile=8), dict(words=8, lazy=True, tile=4), dict(words=8, lazy=True, tile=8),
+              dict(words=8, lazy=True, shuffle=True, tile=4), dict(words=8, shuffle=True, tile=8),
+              dict(words=8, lazy=True, moddown8=True, tile=4), dict(words=16, moddown8=True, tile=8),
+              dict(words=8, lazy=True, moddown8=True, modup8=True, inverse8=True, tile=4),
+              dict(words=16, modup8=True, tile=8), dict(words=16, inverse8=True, tile=8)]
+    for sh in shapes:
+        sh = dict(sh)
+        tile, words = sh.pop("tile"), sh.pop("words")
+        ctx.set_inner_shape(words, **sh)
         ctx.set_tile(tile)
-        what = (f"dnum {dnum}, inner {words} words, lazy {lazy}, shuffle {shfl}, ModDown 8 {md8}, ModUp 8 {mu8}, "
-                f"tile {tile}")
+        what = f"dnum {dnum}, inner {words} words, {sh}, tile {tile}"
         check(ctx, ctx.hmult(evk, a, b), want[("hmult", 23)], what + ", hmult")
-        if words == 8 or md8 or mu8:
+        if words == 8 or sh:
             check(ctx, ctx.rotate(evk, ctx.drop(a, 8), oj.ROT), want[("rot", 8)], what + ", rotation level 8")
             check(ctx, ctx.hmult(evk, ctx.drop(a, 1), b), want[("hmult", 1)], what + ", hmult level 1")
     ctx.set_inner_shape(8, True, False, True)  # the defaults
