@@ -152,6 +152,47 @@ __global__ void __launch_bounds__(PassShape<S, SUB>::THREADS, PassShape<S, SUB>:
     for (int k = 0; k < P::E; k++) d2[it * d2_stride + base + P::T * k] = x[k];
 }
 
+// the automorphism with 8 words per thread (N = 2^15, 2^16), one warp per chunk: the
+// Galois permutation into the storage addresses of natural words 8 h + k, then (poly 1)
+// the first inverse pass, which leaves in natural order (words h + 32 k)
+template <int SUB>
+__global__ void __launch_bounds__(32 * SUB, SUB == 8 ? 4 : 8)
+    k_automorph_ic8(ItemPtrs ip, uint64_t *__restrict__ d2, uint64_t *__restrict__ d2n,
+                    const PrimeC *__restrict__ pc, const Tw *__restrict__ twi, int logN, int nl, uint64_t gal,
+                    size_t pstride, size_t d2_stride)
+{
+    __shared__ uint64_t ex_all[SUB * 256];
+    const int N = 1 << logN;
+    const int row = blockIdx.y, it = row / (2 * nl), r2 = row - it * 2 * nl, poly = r2 / nl, i = r2 - poly * nl;
+    const int h = threadIdx.x & 31, sub = threadIdx.x >> 5;
+    const int g = blockIdx.x * SUB + sub;
+    const size_t o = (size_t)i * N;
+    const uint64_t *src = ip.in0[it] + (size_t)poly * pstride + o;
+    uint64_t x[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        // natural word n = 256 g + 8 h + k holds the evaluation at psi^(2 brv(n) + 1); sigma_g
+        // moves it from psi^(g (2 brv(n) + 1))
+        const uint32_t n = (uint32_t)(g * 256 + 8 * h + k);
+        const uint32_t bk = __brev(n) >> (32 - logN);
+        const uint64_t e = ((2ull * bk + 1) * gal) & (2ull * N - 1);
+        x[k] = src[eval_address(__brev((uint32_t)((e - 1) >> 1)) >> (32 - logN), logN)];
+    }
+    const size_t base = o + (size_t)g * 256;
+    if (poly == 0) {  // block-uniform
+#pragma unroll
+        for (int k = 0; k < 8; k++) ip.out[it][base + addr16(8 * h + k)] = x[k];
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) d2n[it * d2_stride + base + addr16(8 * h + k)] = x[k];
+    const Tw *T = twi + (size_t)i * N;
+    const size_t tg = (size_t)(N >> 8) + g;
+    chunks_inv_core8(x, ex_all + sub * 256, h, [&](int m, int j) { return ldtw(T + m * tg + j); }, pc[i].q);
+#pragma unroll
+    for (int k = 0; k < 8; k++) d2[it * d2_stride + base + h + 32 * k] = x[k];
+}
+
 template <int S, int ALPHA, int SUB>
 __global__ void __launch_bounds__(PassShape<S, SUB>::THREADS, 2)
     k_modup_cols(const uint64_t *__restrict__ y, uint64_t *__restrict__ ext, const uint64_t *__restrict__ ks,
@@ -691,6 +732,15 @@ std::vector<CtObj *> ev_rotate_batch(Ctx &c, const EvkObj &k, const std::vector<
         }
         {
             ProfScope _ps(c, "automorph", (uint64_t)B * 5 * (lv + 1), (uint64_t)B * 2 * (lv + 1));  // reads a
+            if (ntt_s_chunk(c.logN) == 8 && c.inv_words == 8) {  // 8 words per thread
+                auto launch8 = [&](auto bv) {
+                    constexpr int SUB = decltype(bv)::value;
+                    launch_on(c, k_automorph_ic8<SUB>, dim3(c.N / (256 * SUB), B * 2 * (lv + 1)), 32 * SUB, 0, ip,
+                        c.ws_d2, c.ws_d2n, c.d_pc, c.d_twi, c.logN, lv + 1, galois_elt(c, rr), ps, ws.d2);
+                };
+                if (pass_sub(c, 8, B * (lv + 1)) >= 16) launch8(std::integral_constant<int, 8>{});
+                else launch8(std::integral_constant<int, 4>{});
+            } else
             dispatch_pass(c, ntt_s_chunk(c.logN), B * (lv + 1), [&](auto sv, auto bv) {
                 constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
                 launch_on(c, k_automorph_ic<S, SUB>, grid_s(c, S, SUB, B * 2 * (lv + 1)),
