@@ -137,12 +137,12 @@ int ppst_ctx_set_pass_blocks(ppst_ctx *ctx, uint32_t min_blocks);
  * in 128 bits and reduces once per word; bit 1 (8 words only) exchanges the
  * transform's words between the rounds by warp shuffles instead of through
  * shared memory; bit 2 runs ModDown's CHUNKS transform pass with 8 words per
- * thread as well, bit 3 the COLS passes of ModUp and ModDown, bit 4 the first
- * inverse pass (the tensor product's and the plain inverse transforms')
- * (N = 2^15, 2^16).
- * Default: 8 words, flags 5 (lazy accumulation, 8-word ModDown: the fastest
- * measured at N = 2^16). Speed only, never results. PPST_E_ARG for other
- * values. */
+ * thread as well, bit 3 ModUp's COLS pass when its grid is small (fewer than
+ * 456 blocks of the 16-word form: low levels), bit 4 the first inverse pass
+ * (the tensor product's, the automorphism's and the plain inverse
+ * transforms') (N = 2^15, 2^16). Default: 8 words, flags 29 (all but the
+ * shuffle exchanges: the fastest measured at N = 2^16). Speed only, never
+ * results. PPST_E_ARG for other values. */
 int ppst_ctx_set_inner_shape(ppst_ctx *ctx, uint32_t words_per_thread, uint32_t flags);
 /* Failure-detection self-test (no counterpart in the paper): launches one block
  * that waits on a shared-memory barrier nothing completes, bounded by timeout_us

@@ -182,8 +182,9 @@ struct Ctx {
     bool inner_lazy = true;  // 8 words: accumulate the key products in 128 bits, reduce once
     bool inner_shfl = false; // 8 words: the transform's exchanges by warp shuffles instead of shared memory
     int md_words = 8;        // words per thread of ModDown's last (CHUNKS) pass: 8 (used at N >= 2^15) or 16
-    int modup_words = 16;    // words per thread of the COLS passes of ModUp and ModDown: 16, or 8 at N >= 2^15
-    int inv_words = 16;      // words per thread of the first inverse pass (tensor, plain inverse transforms)
+    int modup_words = 8;     // ModUp's COLS pass: 8 words per thread on small grids (N >= 2^15), or always 16
+    int inv_words = 8;       // words per thread of the first inverse pass (tensor, automorphism, plain
+                             // inverse transforms): 8 (used at N >= 2^15) or 16
 
     size_t ct_words() const { return (size_t)2 * (L + 1) * N; }
     size_t ext_rows() const { return (size_t)(L + 1 + K); }

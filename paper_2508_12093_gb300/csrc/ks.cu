@@ -555,7 +555,9 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
         uint64_t targets = 0;
         for (int j = 0; j < nd; j++) targets += E_ext - (std::min((j + 1) * c.alpha, level + 1) - j * c.alpha);
         ProfScope _ps(c, "modup_cols", (uint64_t)B * ((level + 1) + targets));  // limbs read once + written
-        if (ntt_s_rows(c.logN) == 8 && c.modup_words == 8) {  // 8 words per thread, 8 or 4 columns per block
+        // 8 words per thread for grids that would leave SMs idle with 16 (below 3 x 152 blocks of the
+        // 16-column form: low levels, few digits), 8 or 4 columns per block
+        if (ntt_s_rows(c.logN) == 8 && c.modup_words == 8 && (long)(c.N >> 12) * targets * B < 456) {
             dispatch_a(c.alpha, [&](auto av) {
                 constexpr int A = decltype(av)::value;
                 auto launch8 = [&](auto bv) {

@@ -83,48 +83,6 @@ __global__ void __launch_bounds__(PassShape<S, SUB>::THREADS, 2)
     for (int kk = 0; kk < P::E; kk++) out[(size_t)(P::E * h + kk) * C + g] = x[kk];
 }
 
-// the same pass with 8 words per thread (N = 2^15, 2^16): SUB columns per block
-template <bool RESC, int KT, int SUB>
-__global__ void __launch_bounds__(32 * SUB, SUB == 8 ? 3 : 6)
-    k_md_cols8(const uint64_t *__restrict__ acc, const uint64_t *__restrict__ top, uint64_t *__restrict__ z,
-               const uint64_t *__restrict__ hMP, const MdC *__restrict__ mdc, const PrimeC *__restrict__ pc,
-               const Tw *__restrict__ tw, int logN, int level, int nl, int L, int K, size_t ext_stride,
-               size_t z_stride, Ws ws)
-{
-    __shared__ uint64_t sm[SUB * 256];
-    const int N = 1 << logN, C = N >> 8;
-    const int it = blockIdx.y / (2 * nl), rem = blockIdx.y - it * 2 * nl;
-    const int k = rem / nl, i = rem - k * nl;
-    const PrimeC p = pc[i];
-    const MdC mc = mdc[i];
-    __shared__ uint64_t f[16];
-    if (threadIdx.x < K) f[threadIdx.x] = hMP[(size_t)threadIdx.x * (L + 1) + i];
-    __syncthreads();
-    const uint64_t ql = pc[level].q;
-    const int sub = threadIdx.x % SUB, h = threadIdx.x / SUB;
-    const int g = blockIdx.x * SUB + sub;
-    const uint64_t *ym = acc + it * ws.acc + (size_t)k * ext_stride + (size_t)(level + 1) * N + g;
-    const uint64_t *tk = top + it * ws.top + (size_t)k * N + g;
-    uint64_t x[8];
-    bconv_words<KT, 8, 32>(x, ym, f, K, N, C, h, p);
-#pragma unroll
-    for (int kk = 0; kk < 8; kk++) {
-        uint64_t v = csub(shoup(x[kk], mc.pinv.w, mc.pinv.s, p.q), p.q);
-        if (RESC) {
-            const uint64_t tv = tk[(size_t)(h + 32 * kk) * C];
-            uint64_t r = csub(shoup(tv, 1, p.w64, p.q), p.q);
-            if (tv > (ql >> 1)) r = sub_mod(r, mc.qmod, p.q);
-            v = add_mod(v, r, p.q);
-        }
-        x[kk] = v;
-    }
-    const Tw *T = tw + (size_t)i * N;
-    cols_fwd_core8<SUB>(x, sm, h, sub, [&](int m, int jj) { return ldtw(T + m + jj); }, p.q);
-    uint64_t *out = z + it * ws.conv + (size_t)k * z_stride + (size_t)i * N;
-#pragma unroll
-    for (int kk = 0; kk < 8; kk++) out[(size_t)(8 * h + kk) * C + g] = x[kk];
-}
-
 // CHUNKS pass of z and the output combine:
 //   RESC:  out_i = d_i q_l^-1 + acc_i (P^-1 q_l^-1) - Z_i q_l^-1     (d = in0[item])
 //   else:  out_i = add_i + acc_i P^-1 - Z_i        (add = in0[item] for c0, 0 for c1)
@@ -443,18 +401,6 @@ void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip)
     }
     {
         ProfScope _ps(c, "moddown_cols", (uint64_t)B * (2 * c.K + (RESC ? 2 : 0) + 2 * nl));
-        if (ntt_s_rows(c.logN) == 8 && c.modup_words == 8) {  // 8 words per thread, 8 or 4 columns per block
-            dispatch_a(c.K, [&](auto kv) {
-                constexpr int KT = decltype(kv)::value;
-                auto launch8 = [&](auto bv) {
-                    constexpr int SUB = decltype(bv)::value;
-                    launch_on(c, k_md_cols8<RESC, KT, SUB>, grid_s(c, 8, SUB, B * 2 * nl), 32 * SUB, 0, c.ws_acc,
-                        c.ws_top, c.ws_conv, hMP, mdc, c.d_pc, c.d_twf, c.logN, level, nl, c.L, c.K, es, ps, ws);
-                };
-                if (pass_sub(c, 8, B * 2 * nl) >= 16) launch8(std::integral_constant<int, 8>{});
-                else launch8(std::integral_constant<int, 4>{});
-            });
-        } else
         dispatch_pass(c, ntt_s_rows(c.logN), B * 2 * nl, [&](auto sv, auto bv) {
             constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
             dispatch_a(c.K, [&](auto kv) {

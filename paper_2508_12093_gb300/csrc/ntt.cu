@@ -183,15 +183,14 @@ void ntt_inv_mul(Ctx &c, const LimbMap &m, const Tw *outmul)
             if (pass_sub(c, 8, m.count()) >= 16) launch8(std::integral_constant<int, 8>{});
             else launch8(std::integral_constant<int, 4>{});
             check_launch("ntt_chunks_inv8");
-            ntt_inv_cols_mul(c, m, outmul);
-            return;
+        } else {
+            dispatch_pass(c, ntt_s_chunk(c.logN), m, [&](auto sv, auto bv) {
+                constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
+                launch_on(c, k_ntt_inv_chunks<S, SUB>, pass_grid<S, SUB>(c, m), PassShape<S, SUB>::THREADS, 0, m,
+                    c.d_pc, c.d_twi, c.logN);
+            });
+            check_launch("ntt_chunks_inv");
         }
-        dispatch_pass(c, ntt_s_chunk(c.logN), m, [&](auto sv, auto bv) {
-            constexpr int S = decltype(sv)::value, SUB = decltype(bv)::value;
-            launch_on(c, k_ntt_inv_chunks<S, SUB>, pass_grid<S, SUB>(c, m), PassShape<S, SUB>::THREADS, 0, m,
-                c.d_pc, c.d_twi, c.logN);
-        });
-        check_launch("ntt_chunks_inv");
     }
     ntt_inv_cols_mul(c, m, outmul);
 }

@@ -66,7 +66,7 @@ def test_every_dnum_full_size(dnum):
         if words == 8 or sh:
             check(ctx, ctx.rotate(evk, ctx.drop(a, 8), oj.ROT), want[("rot", 8)], what + ", rotation level 8")
             check(ctx, ctx.hmult(evk, ctx.drop(a, 1), b), want[("hmult", 1)], what + ", hmult level 1")
-    ctx.set_inner_shape(8, True, False, True)  # the defaults
+    ctx.set_inner_shape(8, lazy=True, moddown8=True, modup8=True, inverse8=True)  # the defaults
     ctx.set_tile(4)
     # the block shapes the default picks elsewhere: 4 sub-transforms per block at
     # the top level, 16 at level 1
