@@ -88,3 +88,35 @@ def test_batched_workload_shape():
             assert j == i + 1 and i % 2 == 0 and q[3]["B_x"] == 20.0 and q[3]["B_y"] == 1.0
         else:
             assert q[3]["B_x"] == (20.0 if q[4][0] % 2 == 0 else 1.0)
+
+
+def test_autotuner_shapes_and_apply():
+    """Every measured kernel shape has its own name, and applying a tuned row sets
+    exactly its inner-product shape, tile and block-shape threshold (a stand-in
+    context records the calls)."""
+    from paper_2508_12093_gb300 import autotune
+    names = [autotune.shape_name(s) for s in autotune.INNER]
+    assert len(set(names)) == len(names)
+    assert all(s["tile"] in autotune.TILES and s["words"] in (8, 16) for s in autotune.INNER)
+
+    class Rec:
+        def __init__(self):
+            self.calls = []
+
+        def set_inner_shape(self, words, **flags):
+            self.calls.append(("shape", words, tuple(sorted(flags.items()))))
+
+        def set_tile(self, t):
+            self.calls.append(("tile", t))
+
+        def set_pass_blocks(self, b):
+            self.calls.append(("blocks", b))
+
+    r = Rec()
+    autotune.apply(r, {"inner": dict(words=8, lazy=True, inverse8=True, tile=4), "pass_min_blocks": 912})
+    want_flags = tuple(sorted({f: f in ("lazy", "inverse8") for f in autotune.FLAGS}.items()))
+    assert r.calls == [("shape", 8, want_flags), ("tile", 4), ("blocks", 912)]
+    r = Rec()
+    autotune.apply(r, {"tile": 16})  # a row from before the shape search: the 16-word form
+    assert r.calls[0] == ("shape", 16, tuple(sorted({f: False for f in autotune.FLAGS}.items())))
+    assert r.calls[1] == ("tile", 16) and len(r.calls) == 2
