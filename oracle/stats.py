@@ -12,7 +12,8 @@ TEST INFRASTRUCTURE (oracle). The schedules here follow the paper:
 * Mean(x, B) and Variance(x, B) with the pre-normalisation constants folded
   into the plaintext multipliers (Sec. 6.1, Eq. 2).
 * ZNorm (Alg. 4), Kurt (Alg. 5), Skew (Sec. 6: mirrors Alg. 5 with the third
-  moment), CV (Alg. 6 for a positive mean, without Sign), PCC (Sec. 6.5).
+  moment), CV (Alg. 6 for a positive mean, without Sign), the sign-aware CV
+  (Alg. 6 with Sign read as mu * CryptoInvSqrt(mu^2)), PCC (Sec. 6.5).
 
 Readings where the paper is silent (the same on the GPU side):
 * Chebyshev evaluation is baby-step giant-step in the Chebyshev basis with
@@ -246,8 +247,26 @@ def cv(ev, cts, n, B, k, t):
     return ev.hmult(std, mu_inv)
 
 
+def cv_signed(ev, cts, n, B, k, t):
+    """Alg. 6 with its Sign, for a mean of either sign: CV = Std(x) * (1 / |mu|) *
+    sign(mu). Sign(mu) is mu * CryptoInvSqrt(mu^2, B^2) = mu / |mu| (the identity
+    sign(x) = x / sqrt(x^2) on the inverse root that the method already has), and
+    the inverse of the sign-corrected mean, CryptoInvSqrt(mu * sign(mu), B)^2 =
+    1 / |mu|, is that same CryptoInvSqrt(mu^2, B^2): one inverse-root chain of the
+    mean in place of Alg. 6's Sign (a depth-32 minimax polynomial) followed by a
+    second chain. The input (mu / B)^2 lies in (0, 1] for |mu| <= B; Alg. 6's line
+    order is kept: tmp = Std * mu_inv, then CV = tmp * sign."""
+    R = ev.rotsum(col_sum(ev, cts))
+    mu = ev.mul_const(R, 1.0 / n)
+    muB = ev.mul_const(R, 1.0 / (B * n))
+    mu_inv = crypto_inv_sqrt(ev, ev.hmult(muB, muB), B * B, k, t)   # 1 / |mu|
+    sign = ev.hmult(mu, mu_inv)
+    std = crypto_sqrt(ev, variance(ev, cts, n, B, R), B * B, k)
+    return ev.hmult(ev.hmult(std, mu_inv), sign)
+
+
 def pcc(ev, xcts, ycts, n, Bx, By, k, t):
-    """Sec. 6.5: Cov(x, y) * CryptoInvSqrt(Var(x,Bx),Bx^2) * CryptoInvSqrt(Var(y,By),By^2)."""
+    """Sec. 6.5:Cov(x, y) * CryptoInvSqrt(Var(x,Bx),Bx^2) * CryptoInvSqrt(Var(y,By),By^2)."""
     Rx = ev.rotsum(col_sum(ev, xcts))
     Ry = ev.rotsum(col_sum(ev, ycts))
     mux = ev.mul_const(Rx, 1.0 / n)

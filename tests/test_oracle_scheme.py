@@ -277,6 +277,49 @@ def test_statistics_schedules_simulated(n, nct):
     assert abs(r.v[0] / ref_p["pcc"] - 1) < 1e-4
 
 
+@pytest.mark.parametrize("mu", [-4.0, -1.5, 3.0])
+def test_sign_aware_cv_simulated(mu):
+    """Alg. 6 with Sign, through the noise-free simulator, on normal columns of
+    either sign (3000 rows over three ciphertexts): the result is Std / mu,
+    negative for a negative mean, within 1e-4 of scipy's variation; negating the
+    column negates the result exactly (Sign flips, 1/|mu| and Std do not); for a
+    positive mean it agrees with the positive-mean CV; it costs one level more
+    than that CV (18 of 23 at degree 127 + 3 Newton steps)."""
+    sp = pytest.importorskip("scipy.stats")
+    S, n, B = 1024, 3000, 8.0
+    ev = sim_for(S=S, levels=24)
+    x = workloads.normal_column(n, seed=5, mu=mu, sigma=2.0)
+    cts = [ev.encrypt(x[i * S:(i + 1) * S]) for i in range(3)]
+    neg = [ev.encrypt(-x[i * S:(i + 1) * S]) for i in range(3)]
+    r = stats.cv_signed(ev, cts, n, B, 7, 3)
+    ref = sp.variation(x)
+    assert math.copysign(1.0, ref) == math.copysign(1.0, mu)
+    assert abs(r.v[0] / ref - 1) < 1e-4
+    assert stats.cv_signed(ev, neg, n, B, 7, 3).v[0] == -r.v[0]
+    assert cts[0].level - r.level == 18
+    if mu > 0:
+        p = stats.cv(ev, cts, n, B, 7, 3)
+        assert abs(p.v[0] / r.v[0] - 1) < 1e-4 and cts[0].level - p.level == 17
+
+
+def test_sign_aware_cv_on_ckks():
+    """The sign-aware CV on the exact CKKS oracle (N = 2^12, 15 Q primes: the
+    depth 14 of degree 31 + 2 Newton steps) for a negative-mean column spread
+    over two ciphertexts with a ragged tail: negative, within 1e-3 of FP64, and
+    the schedule ends at level 0."""
+    prm = ckks.Params(log_n=12, n_q=15, n_p=1, dnum=15, q0_bits=60, q_bits=40, p_bits=60, log_scale=40)
+    c = ckks.Ckks(prm)
+    keys = c.keygen(2, rotations=[1 << i for i in range(prm.log_n - 1)])
+    n = prm.S + 700
+    x = workloads.normal_column(n, seed=8, mu=-3.0, sigma=3.0)
+    cts = c.encrypt_column(keys["pk"], x, 5)
+    r = stats.cv_signed(stats.CkksEv(c, keys), cts, n, 6.0, 5, 2)
+    assert r.level == 0
+    got = c.decrypt(keys["s"], r)[0]
+    ref = stats.plain_stats(x)["cv"]
+    assert ref < 0 and abs(got / ref - 1) < 1e-3
+
+
 def test_znorm_on_ckks_cfg1_shape():
     """Full Z-score schedule on the exact CKKS oracle, N = 2^12, 12 Q primes
     (depth 11), within 1e-3 of FP64 plaintext."""

@@ -11,6 +11,8 @@ available; these stand-ins have the shapes the paper describes:
 * a binary attribute (smoker-like) x ~ Bernoulli(0.2) and a charge-like
   y = lognormal(9, 0.6) + 20000 x + N(0, 3000^2), also scaled by 1/1000;
 * uniform [0, 1) columns (toy case), uniform [0, 100] / [0, 20] (Sec. 7.3);
+* normal columns with a negative mean (Sec. 6.4: the mean in CV's
+  denominator may be negative);
 * the inverse-square-root grid of Sec. 7.2: 16,384 points evenly spaced in
   [0.001, 1] and 16,384 in [1, 100].
 """
@@ -38,6 +40,11 @@ def uniform_column(n, seed=SEEDS["data"], lo=0.0, hi=1.0):
 
 def lognormal_column(n, seed=SEEDS["data"], mu=9.0, sigma=0.9, scale=1e-3):
     return np.random.default_rng(seed).lognormal(mu, sigma, n) * scale
+
+
+def normal_column(n, seed=SEEDS["data"], mu=-4.0, sigma=2.0):
+    """Normal values whose mean may be negative (the sign-aware CV's input)."""
+    return np.random.default_rng(seed).normal(mu, sigma, n)
 
 
 def pcc_pair(n, seed=SEEDS["data"], p=0.2, scale=1e-3):
