@@ -91,7 +91,12 @@ typedef enum {
     PPST_CV = 1,     /* Alg. 6 for a positive mean (no Sign): scalar        */
     PPST_SKEW = 2,   /* third-moment mirror of Alg. 5: scalar               */
     PPST_KURT = 3,   /* Alg. 5 (plain, not excess, kurtosis): scalar        */
-    PPST_PCC = 4     /* Sec. 6.5, two columns: scalar                       */
+    PPST_PCC = 4,    /* Sec. 6.5, two columns: scalar                       */
+    PPST_CV_SIGNED = 5 /* Alg. 6 with Sign, a mean of either sign: scalar.
+                        * Sign(mu) = mu * CryptoInvSqrt(mu^2, B^2), and the
+                        * inverse of the sign-corrected mean is that same root
+                        * (1/|mu|): one level more than PPST_CV. Needs
+                        * |Mean| / B in (0, 1] besides Var / B^2 in (0, 2]. */
 } ppst_stat;
 
 /* Per-query options. B_x, B_y: pre-normalisation bounds (Sec. 6.1, Eq. 2):

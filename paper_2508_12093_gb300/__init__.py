@@ -16,10 +16,11 @@ import weakref
 import numpy as np
 
 from . import _lib
-from ._lib import (ERRORS, PPST_CV, PPST_KURT, PPST_PCC, PPST_SKEW, PPST_ZSCORE, lib, ppst_allocator,  # noqa: F401
+from ._lib import (ERRORS, PPST_CV, PPST_CV_SIGNED, PPST_KURT, PPST_PCC, PPST_SKEW, PPST_ZSCORE, lib, ppst_allocator,  # noqa: F401
                    ppst_params, ppst_qopts, ppst_report)
 
-STATS = {"zscore": PPST_ZSCORE, "cv": PPST_CV, "skew": PPST_SKEW, "kurt": PPST_KURT, "pcc": PPST_PCC}
+STATS = {"zscore": PPST_ZSCORE, "cv": PPST_CV, "skew": PPST_SKEW, "kurt": PPST_KURT, "pcc": PPST_PCC,
+         "cv_signed": PPST_CV_SIGNED}
 
 
 class PpstError(RuntimeError):

@@ -19,7 +19,7 @@ PP = P(c_void_p)
 PPST_OK = 0
 ERRORS = {-1: "PPST_E_ARG", -2: "PPST_E_DEPTH", -3: "PPST_E_SCALE", -4: "PPST_E_OOM", -5: "PPST_E_BUDGET",
           -6: "PPST_E_CUDA", -7: "PPST_E_TIMEOUT", -8: "PPST_E_STATE"}
-PPST_ZSCORE, PPST_CV, PPST_SKEW, PPST_KURT, PPST_PCC = 0, 1, 2, 3, 4
+PPST_ZSCORE, PPST_CV, PPST_SKEW, PPST_KURT, PPST_PCC, PPST_CV_SIGNED = 0, 1, 2, 3, 4, 5
 
 
 class ppst_params(ctypes.Structure):

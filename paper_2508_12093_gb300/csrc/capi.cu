@@ -57,7 +57,7 @@ namespace ppst {
 void validate_query(const Ctx &cc, const QueryIn &q)
 {
     const Ctx *c = &cc;
-    REQ(q.stat >= PPST_ZSCORE && q.stat <= PPST_PCC, "unknown statistic");
+    REQ(q.stat >= PPST_ZSCORE && q.stat <= PPST_CV_SIGNED, "unknown statistic");
     REQ(ok(q.x, TAG_COL) && q.x->ctx == c, "bad column");
     if (q.stat == PPST_PCC) {
         REQ(ok(q.y, TAG_COL) && q.y->ctx == c && q.y->n == q.x->n && q.y->cts.size() == q.x->cts.size(),

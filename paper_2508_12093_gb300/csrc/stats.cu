@@ -9,7 +9,8 @@
 //  * Mean(x, B), Variance(x, B) with the 1/B constants folded into the
 //    plaintext multipliers (Sec. 6.1, Eq. 2): Variance costs depth 2.
 //  * ZNorm (Alg. 4), Kurt (Alg. 5), Skew (third-moment mirror of Alg. 5),
-//    CV (Alg. 6 for a positive mean, no Sign), PCC (Sec. 6.5).
+//    CV (Alg. 6 for a positive mean, no Sign), the sign-aware CV (Alg. 6 with
+//    Sign(mu) = mu * CryptoInvSqrt(mu^2, B^2)), PCC (Sec. 6.5).
 // Where the paper is silent: the Chebyshev sum is evaluated baby-step
 // giant-step in the Chebyshev basis (T_2i = 2 T_i^2 - 1, T_2i+1 = 2 T_i T_i+1
 // - T_1, giants T_2^m, recursive division by T_n); a leaf sum is one linear
@@ -755,6 +756,21 @@ H cv(Ev &ev, const Col &x, size_t n, double B, int k, int t, const void *kx)
     return ev.hmult(std_, mu_inv);
 }
 
+// Alg. 6 with Sign, for a mean of either sign: Sign(mu) = mu * CryptoInvSqrt(mu^2, B^2)
+// (sign(x) = x / sqrt(x^2)), and the inverse of the sign-corrected mean,
+// CryptoInvSqrt(mu sign(mu), B)^2 = 1 / |mu|, is that same inverse root; the lines
+// keep Alg. 6's order: tmp = Std * mu_inv, CV = tmp * sign. One level more than cv.
+H cv_signed(Ev &ev, const Col &x, size_t n, double B, int k, int t, const void *kx)
+{
+    H R = col_rsum(ev, x, kx);
+    H mu = ev.mul_const(R, 1.0 / (double)n);
+    H muB = ev.mul_const(R, 1.0 / (B * (double)n));
+    H mu_inv = crypto_inv_sqrt(ev, ev.hmult(muB, muB), B * B, k, t);  // 1 / |mu|
+    H sign = ev.hmult(mu, mu_inv);
+    H std_ = crypto_sqrt(ev, col_var(ev, x, n, B, R, kx), B * B, k);
+    return ev.hmult(ev.hmult(std_, mu_inv), sign);
+}
+
 H pcc(Ev &ev, const Col &x, const Col &y, size_t n, double Bx, double By, int k, int t, const void *kx,
       const void *ky)
 {
@@ -797,6 +813,7 @@ ResObj *run_one(Ev &ev, const QueryIn &q)
     case PPST_KURT: res.push_back(kurt(ev, x, n, q.o.B_x, kk, tt, q.x)); break;
     case PPST_SKEW: res.push_back(skew(ev, x, n, q.o.B_x, kk, tt, q.x)); break;
     case PPST_CV: res.push_back(cv(ev, x, n, q.o.B_x, kk, tt, q.x)); break;
+    case PPST_CV_SIGNED: res.push_back(cv_signed(ev, x, n, q.o.B_x, kk, tt, q.x)); break;
     case PPST_PCC: res.push_back(pcc(ev, x, view(*q.y), n, q.o.B_x, q.o.B_y, kk, tt, q.x, q.y)); break;
     default: throw_err(PPST_E_ARG, "unknown statistic");
     }

@@ -2,6 +2,7 @@
 
     python -m paper_2508_12093_gb300.profcase hmult      # N=2^16, 3 top-level HMult+KS
     python -m paper_2508_12093_gb300.profcase rotate     # N=2^16, 3 top-level rotations
+    python -m paper_2508_12093_gb300.profcase levels     # N=2^16, 2 HMults + 2 rotations at levels 23, 12, 4
     python -m paper_2508_12093_gb300.profcase query      # N=2^16, one kurtosis query
     python -m paper_2508_12093_gb300.profcase batch3     # N=2^16, skew/kurt/CV of three columns, one batch
     python -m paper_2508_12093_gb300.profcase stages [dnum[:shape] ...]  # per-kernel-class times (CUDA events)
@@ -89,6 +90,17 @@ def main(case):
             op()
         for _ in range(3):
             op()
+    elif case == "levels":
+        # each op twice at levels 23, 12 and 4 after one warm-up (for a launch list of
+        # per-kernel durations: the small grids of the low levels are latency-bound)
+        sk, evk = ctx.keygen(2, rotations=[1])
+        a = ctx.encrypt_ints(evk, np.arange(ctx.N, dtype=np.int64) % 1000, 9, 0, 2.0 ** 50)
+        for lv in (23, 12, 4):
+            al = ctx.drop(a, lv)
+            for _ in range(3):
+                ctx.hmult(evk, al, al)
+            for _ in range(3):
+                ctx.rotate(evk, al, 1)
     elif case == "query":
         sk, evk = ctx.keygen(2)
         col = ctx.encrypt_column(evk, workloads.lognormal_column(ctx.S, seed=1), 3)

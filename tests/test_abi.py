@@ -35,6 +35,17 @@ def test_binding_covers_the_header():
     assert set(declared_functions()) == set(_lib.SIGNATURES)
 
 
+def test_statistic_ids_match_the_header():
+    """The binding's statistic ids are the header's ppst_stat values."""
+    from paper_2508_12093_gb300 import _lib, STATS
+    src = open(os.path.join(ROOT, "include", "ppst.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef enum \{([^}]*)\} ppst_stat;", src).group(1)
+    enum = {k: int(v) for k, v in re.findall(r"(PPST_[A-Z_]+)\s*=\s*(\d+)", body)}
+    assert enum == {k: getattr(_lib, k) for k in enum}
+    assert sorted(STATS.values()) == sorted(enum.values())
+
+
 def test_null_and_bad_handles_are_rejected(libppst):
     # argument checks that run before any CUDA call
     from paper_2508_12093_gb300 import _lib

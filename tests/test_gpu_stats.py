@@ -113,6 +113,30 @@ def test_schedule_parity_benchmark_settings(deep, stat):
     assert rep["depth_used"] == {"skew": 19, "kurt": 19, "cv": 17, "zscore": 17, "pcc": 18}[stat]
 
 
+@pytest.mark.parametrize("mu,n,k,t", [(-3.0, 2048 + 301, 5, 2), (-3.0, 2048 + 301, 7, 3), (4.0, 2048, 7, 3),
+                                       (-0.7, 2049, 5, 2)])
+def test_sign_aware_cv_parity(deep, mu, n, k, t):
+    """The sign-aware CV (Alg. 6 with Sign) on normal columns of either sign:
+    result limbs bit-exact against the oracle, the value within 1e-3 of FP64
+    (negative for a negative mean), one level more than the positive-mean CV
+    (depth 18 at degree 127 + 3 Newton steps, in a 19-level chain)."""
+    from oracle import stats as ost
+    ctx, sk, evk, oc, ok = deep
+    B = 6.0
+    x = workloads.normal_column(n, seed=17, mu=mu, sigma=3.0)
+    o, col = shared_column(deep, x, 71)
+    opts = dict(B_x=B, cheb_log2deg=k, newton_steps=t)
+    res = ctx.query(evk, "cv_signed", col, opts=opts)
+    check_same(ctx, res.cts()[0], ost.cv_signed(ost.CkksEv(oc, ok), o, n, B, k, t))
+    v, rep = ctx.decrypt(sk, res)
+    ref = ost.plain_stats(x)["cv"]
+    assert np.sign(v[0]) == np.sign(mu) and abs(v[0] / ref - 1) < TOL, (v[0], ref)
+    _, rp = ctx.decrypt(sk, ctx.query(evk, "cv", col, opts=opts))
+    assert rep["depth_used"] == rp["depth_used"] + 1
+    if (k, t) == (7, 3):
+        assert rep["depth_used"] == 18
+
+
 @pytest.mark.parametrize("n", [2048, 3000])
 def test_pcc_parity_small(deep, n):
     from oracle import stats as ost
@@ -183,6 +207,25 @@ def test_statistics_full_size(big, stat):
     ref = ost.plain_stats(x)[stat]
     assert abs(v[0] / ref - 1) < TOL, (v[0], ref)
     assert rep["level_out"] >= 0
+
+
+@pytest.mark.parametrize("mu", [-4.0, 5.0])
+def test_sign_aware_cv_full_size(big, mu):
+    """N = 2^16: the sign-aware CV of a 32,768-row normal column with a negative
+    or positive mean within 1e-3 of FP64; for the positive mean it agrees with
+    the positive-mean CV."""
+    from oracle import stats as ost
+    ctx, sk, evk = big
+    x = workloads.normal_column(32768, seed=3, mu=mu, sigma=3.0)
+    col = ctx.encrypt_column(evk, x, 7)
+    opts = dict(OPTS16, B_x=8.0)
+    v, rep = ctx.decrypt(sk, ctx.query(evk, "cv_signed", col, opts=opts))
+    ref = ost.plain_stats(x)["cv"]
+    assert abs(v[0] / ref - 1) < TOL, (v[0], ref)
+    assert rep["depth_used"] == 18
+    if mu > 0:
+        p, _ = ctx.decrypt(sk, ctx.query(evk, "cv", col, opts=opts))
+        assert abs(p[0] / v[0] - 1) < TOL
 
 
 def test_pcc_full_size(big):
