@@ -342,10 +342,15 @@ void k_rescale(Ctx &c, const CtObj &a, CtObj &out) { k_rescale_mul(c, a, nullptr
 // ---------------------------------------------------------------------------
 // linear combination with integer weights: out = sum_k m_k ct_k (one level)
 // ---------------------------------------------------------------------------
+// Each thread owns two adjacent words of one limb row and reads them from every
+// term with one 16-byte load; the loads of eight terms are issued before their
+// products are accumulated, so a warp keeps eight independent requests in flight
+// per term group instead of one (the kernel is bound by HBM, 8 (n + 1) bytes a word).
 __global__ void __launch_bounds__(EW_THREADS) k_lincomb_kernel(LinArgs args, uint64_t *__restrict__ out,
                                                                const PrimeC *__restrict__ pc, int N, int nl,
                                                                size_t pstride)
 {
+    constexpr int G = 8;  // terms whose loads are in flight together
     __shared__ uint64_t r[LinArgs::MAXT], rs[LinArgs::MAXT];
     const int row = blockIdx.y, poly = row / nl, i = row - poly * nl;
     const uint64_t q = pc[i].q;
@@ -358,19 +363,35 @@ __global__ void __launch_bounds__(EW_THREADS) k_lincomb_kernel(LinArgs args, uin
         rs[threadIdx.x] = (uint64_t)(((u128)rr << 64) / q);
     }
     __syncthreads();
-    // grid-stride over the row: the weights' residues above are computed once per block
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        const size_t o = (size_t)poly * pstride + (size_t)i * N + c;
-        uint64_t acc = 0;
-        for (int k = 0; k < args.n; k++) acc = add_mod(acc, csub(shoup(args.p[k][o], r[k], rs[k], q), q), q);
-        out[o] = acc;
+    const int c = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (c >= N) return;
+    const size_t o = (size_t)poly * pstride + (size_t)i * N + c;
+    uint64_t a0 = 0, a1 = 0;
+    for (int k0 = 0; k0 < args.n; k0 += G) {
+        ulonglong2 v[G];
+#pragma unroll
+        for (int j = 0; j < G; j++)
+            if (k0 + j < args.n) v[j] = __ldg(reinterpret_cast<const ulonglong2 *>(args.p[k0 + j] + o));
+#pragma unroll
+        for (int j = 0; j < G; j++)
+            if (k0 + j < args.n) {
+                const uint64_t w = r[k0 + j], ws = rs[k0 + j];
+                a0 = add_mod(a0, csub(shoup(v[j].x, w, ws, q), q), q);
+                a1 = add_mod(a1, csub(shoup(v[j].y, w, ws, q), q), q);
+            }
     }
+    *reinterpret_cast<ulonglong2 *>(out + o) = make_ulonglong2(a0, a1);
 }
 
 void k_lincomb(Ctx &c, const LinArgs &args, int level, CtObj &out)
 {
+    // every ciphertext buffer starts on a 256-byte boundary and its limb rows are
+    // whole multiples of N words, so the 16-byte accesses are aligned
+    for (int k = 0; k < args.n; k++)
+        if ((uintptr_t)args.p[k] % 16) throw_err(PPST_E_ARG, "lin_comb: operand not 16-byte aligned");
+    if ((uintptr_t)out.d % 16 || c.N % 2) throw_err(PPST_E_ARG, "lin_comb: output not 16-byte aligned");
     ProfScope _ps(c, "lincomb", (uint64_t)(args.n + 1) * 2 * (level + 1));
-    const dim3 grid(std::max(1, c.N / (EW_THREADS * 8)), 2 * (level + 1));  // 8 words per thread
+    const dim3 grid((c.N / 2 + EW_THREADS - 1) / EW_THREADS, 2 * (level + 1));
     k_lincomb_kernel<<<grid, EW_THREADS, 0, c.stream>>>(args, out.d, c.d_pc, c.N, level + 1, (size_t)(c.L + 1) * c.N);
     check_launch("k_lincomb");
 }

@@ -119,6 +119,13 @@ def test_lin_comb(env):
     coeffs = [0.25, -3.5, 1e-3, 7.0, -0.125]
     for n in (1, 3, 5):
         same(ctx, ctx.lin_comb(glist[:n], coeffs[:n], 2.0 ** 40), oc.lin_comb(olist[:n], coeffs[:n], 2.0 ** 40))
+    # more terms than one group of loads in flight (8), a ragged last group, the maximum (32)
+    rng = np.random.default_rng(12)
+    for n in (8, 9, 20, 32):
+        idx = [k % 5 for k in range(n)]
+        cs = list(rng.uniform(-4, 4, n))
+        same(ctx, ctx.lin_comb([glist[k] for k in idx], cs, 2.0 ** 40),
+             oc.lin_comb([olist[k] for k in idx], cs, 2.0 ** 40))
 
 
 def test_hmult_all_levels(env):
