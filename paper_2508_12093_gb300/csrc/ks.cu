@@ -13,7 +13,11 @@
 //   3. k_inner_chunks: one block per (item, target limb e, 16 chunks) loops over
 //      the digits, finishes the transform in registers (the digit's own limbs
 //      are taken from d in the evaluation domain instead) and accumulates both
-//      key polynomials; the twiddles of prime e are reused by every digit.
+//      key polynomials; the twiddles of prime e are reused by every digit. The
+//      8-word form (k_inner8) also runs ModDown's first inverse pass on the rows
+//      ModDown takes to the coefficient domain (the P rows; in HMult the top
+//      limb l too, after forming d_l + acc_l P^-1), so ModDown starts at their
+//      COLS pass.
 // ModDown (and, in HMult, the rescale after it) is fused the same way. For
 // limb i < l of the HMult output:
 //   out_i = (d_i + acc_i P^-1 - NTT(conv_i P^-1 + [top]_centred mod q_i)) q_l^-1
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(InnerSmem<S, SUB>::THREADS, InnerSmem<S, SUB>:
     constexpr uint32_t TB = SM::TILE * 8;
     const int N = 1 << logN;
     const int it = blockIdx.x % B, tile = blockIdx.x / B;
-    const int e = blockIdx.y;
+    const int e = (int)gridDim.y - 1 - (int)blockIdx.y;
     const int row = e <= level ? e : L + 1 + (e - level - 1);
     const PrimeC p = pc[row];
     const Tw *T = tw + (size_t)row * N;
@@ -400,11 +404,18 @@ struct Inner8Smem {
     static constexpr size_t BYTES = T_OFF + (size_t)TILE * 8;
 };
 
+// Rows e >= inv_from of the accumulators are the ones ModDown takes to the
+// coefficient domain (the P rows, and in HMult the top limb l after u = d_l +
+// acc_l P^-1): they leave through the first (CHUNKS) inverse pass here, on the
+// words already in registers, so ModDown runs only the COLS pass on them. The
+// block rows are taken from the top, so the blocks with the longer epilogue start
+// first. inv_from > level + K turns this off.
 template <int SUB, bool LAZY, bool SHFL>
 __global__ void __launch_bounds__(Inner8Smem<SUB>::THREADS, SUB == 8 ? 2 : 4)
     k_inner8(const uint64_t *__restrict__ ext, const uint64_t *__restrict__ d2n, const uint64_t *__restrict__ key,
-             uint64_t *__restrict__ acc, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw, int logN, int level,
-             int alpha, int L, int K, int nd, size_t ext_stride, int B, Ws ws, int *err)
+             uint64_t *__restrict__ acc, const PrimeC *__restrict__ pc, const Tw *__restrict__ tw,
+             const Tw *__restrict__ twi, int logN, int level, int alpha, int L, int K, int nd, size_t ext_stride,
+             int B, Ws ws, int inv_from, ItemPtrs dtop, Tw pinv, size_t pstride, int *err)
 {
     typedef Inner8Smem<SUB> SM;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -414,7 +425,7 @@ __global__ void __launch_bounds__(Inner8Smem<SUB>::THREADS, SUB == 8 ? 2 : 4)
     constexpr uint32_t TB = SM::TILE * 8;
     const int N = 1 << logN;
     const int it = blockIdx.x % B, tile = blockIdx.x / B;
-    const int e = blockIdx.y;
+    const int e = (int)gridDim.y - 1 - (int)blockIdx.y;
     const int row = e <= level ? e : L + 1 + (e - level - 1);
     const PrimeC p = pc[row];
     const Tw *T = tw + (size_t)row * N;
@@ -501,17 +512,38 @@ __global__ void __launch_bounds__(Inner8Smem<SUB>::THREADS, SUB == 8 ? 2 : 4)
         return;
     }
     uint64_t *o0 = acc + it * ws.acc + (size_t)e * N + t0, *o1 = o0 + krow;
+    if (LAZY) {
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
-        if (LAZY) {  // (hi mod q) 2^64 + lo, then one Montgomery reduction
+        for (int k = 0; k < 8; k++) {  // (hi mod q) 2^64 + lo, then one Montgomery reduction
             const uint64_t h0 = csub(shoup(acc4_hi(u0[k]), 1, p.w64, p.q), p.q);
             const uint64_t h1 = csub(shoup(acc4_hi(u1[k]), 1, p.w64, p.q), p.q);
-            o0[ka[k]] = mont_redc(h0, acc4_lo(u0[k]), p.q, p.qinv);
-            o1[ka[k]] = mont_redc(h1, acc4_lo(u1[k]), p.q, p.qinv);
-        } else {
+            a0[k] = mont_redc(h0, acc4_lo(u0[k]), p.q, p.qinv);
+            a1[k] = mont_redc(h1, acc4_lo(u1[k]), p.q, p.qinv);
+        }
+    }
+    if (e < inv_from) {  // block-uniform
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
             o0[ka[k]] = a0[k];
             o1[ka[k]] = a1[k];
         }
+        return;
+    }
+    if (e == level) {  // HMult's top limb: u_k = d_k[l] + acc_k[l] P^-1 (evaluation domain)
+        const uint64_t *d0 = dtop.in0[it] + (size_t)level * N + t0, *d1 = d0 + pstride;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            a0[k] = add_mod(d0[ka[k]], csub(shoup(a0[k], pinv.w, pinv.s, p.q), p.q), p.q);
+            a1[k] = add_mod(d1[ka[k]], csub(shoup(a1[k], pinv.w, pinv.s, p.q), p.q), p.q);
+        }
+    }
+    const Tw *TI = twi + (size_t)row * N;
+    chunks_inv_core8(a0, ex, h, [&](int m, int jj) { return ldtw(TI + m * tg + jj); }, p.q);
+    chunks_inv_core8(a1, ex, h, [&](int m, int jj) { return ldtw(TI + m * tg + jj); }, p.q);
+#pragma unroll
+    for (int k = 0; k < 8; k++) {  // the inverse pass's output order: word h + 32 k of the chunk
+        o0[sub * SM::M + h + 32 * k] = a0[k];
+        o1[sub * SM::M + h + 32 * k] = a1[k];
     }
 }
 
@@ -542,7 +574,11 @@ void wait_selftest(Ctx &c, uint32_t timeout_us)
 // stages 1-3 for B items: d (limbs 0..level) of item b in the evaluation domain
 // in ws_d2n[b] and (to be transformed) in ws_d2[b]; accumulators to ws_acc[b]
 // d2 (every item) has been through the first inverse pass (k_tensor_ic / k_automorph_ic)
-static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
+// Returns true when the inner product also ran ModDown's first inverse pass on
+// its rows (the 8-word kernel): resc selects HMult's rows (the top limb l, whose
+// u = d_l + acc_l P^-1 takes d from dtop.in0, and the P rows) or a rotation's (the
+// P rows).
+static bool ks_modup_inner(Ctx &c, int level, const Swk &key, int B, bool resc, const ItemPtrs &dtop)
 {
     const Ws ws = ws_strides(c);
     const int nd = c.ndigits(level), E_ext = level + 1 + c.K;
@@ -611,13 +647,16 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
                                            (int)SM::BYTES));
             attr_set = true;
         }
+        const Tw pinv = c.md_const[(size_t)level * (c.L + 1) + level].pinv;
         launch_on(c, k_inner8<SUB, LAZY, SHFL>, grid, SM::THREADS, SM::BYTES, c.ws_ext, c.ws_d2n, key.d,
-            c.ws_acc, c.d_pc, c.d_twf, c.logN, level, c.alpha, c.L, c.K, nd, es, B, ws, c.d_err);
+            c.ws_acc, c.d_pc, c.d_twf, c.d_twi, c.logN, level, c.alpha, c.L, c.K, nd, es, B, ws,
+            resc ? level : level + 1, dtop, pinv, (size_t)(c.L + 1) * c.N, c.d_err);
     };
     auto launch8 = [&](auto subv, auto lazyv) {
         if (c.inner_shfl) launch8s(subv, lazyv, std::true_type{});
         else launch8s(subv, lazyv, std::false_type{});
     };
+    bool fused = false;
     dispatch_s(ntt_s_chunk(c.logN), [&](auto sv) {
         constexpr int S = decltype(sv)::value;
         // the context's tile, halved (down to 4 chunks) while the grid would leave SMs idle
@@ -631,6 +670,7 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
                 if (c.inner_lazy) launch8(std::integral_constant<int, 4>{}, std::true_type{});
                 else launch8(std::integral_constant<int, 4>{}, std::false_type{});
             }
+            fused = true;
             return;
         }
         switch (tile) {
@@ -640,6 +680,7 @@ static void ks_modup_inner(Ctx &c, int level, const Swk &key, int B)
         }
     });
     check_launch("k_inner_chunks");
+    return fused;
 }
 
 // HMult of B pairs (each pair at its own min level; all pairs share that level):
@@ -684,14 +725,14 @@ std::vector<CtObj *> ev_hmult_batch(Ctx &c, const EvkObj &k, const std::vector<c
             });
             check_launch("k_tensor_ic");
         }
-        ks_modup_inner(c, lv, k.relin, B);
         ItemPtrs op{};
         for (int i = 0; i < B; i++) {
             o[i] = ct_new(c, lv - 1, (as[i]->scale * bs[i]->scale) / (double)c.primes[lv]);
             op.in0[i] = t[i]->d;
             op.out[i] = o[i]->d;
         }
-        ks_moddown<true>(c, lv, B, op);
+        const bool fused = ks_modup_inner(c, lv, k.relin, B, true, op);
+        ks_moddown<true>(c, lv, B, op, fused);
     } catch (...) {
         for (CtObj *x : t) ct_free(x);
         for (CtObj *x : o) ct_free(x);
@@ -751,13 +792,13 @@ std::vector<CtObj *> ev_rotate_batch(Ctx &c, const EvkObj &k, const std::vector<
             });
             check_launch("k_automorph_ic");
         }
-        ks_modup_inner(c, lv, it->second, B);
         ItemPtrs op{};
         for (int i = 0; i < B; i++) {
             op.in0[i] = o[i]->d;  // sigma(c0), added to ModDown(acc_0) in place
             op.out[i] = o[i]->d;
         }
-        ks_moddown<false>(c, lv, B, op);
+        const bool fused = ks_modup_inner(c, lv, it->second, B, false, op);
+        ks_moddown<false>(c, lv, B, op, fused);
     } catch (...) {
         for (CtObj *x : o) ct_free(x);
         throw;

@@ -93,6 +93,6 @@ void dispatch_pass(const Ctx &c, int s, int rows, F &&f)
 
 // ModDown (+ rescale) of the accumulators of B items (ks_down.cu)
 template <bool RESC>
-void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip);
+void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip, bool first_pass_done);
 
 }  // namespace ppst

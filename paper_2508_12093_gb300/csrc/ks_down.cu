@@ -369,8 +369,10 @@ void ks_rescale(Ctx &c, const CtObj &a, const uint64_t *top, uint64_t *z, const 
 // ModDown of ws_acc (+ rescale) for B items. RESC: out[b] (level-1) =
 // rescale(in0[b] + ModDown(acc[b])), in0 = the tensor product; else out[b].c0 =
 // in0[b] + ModDown(acc_0), out[b].c1 = ModDown(acc_1).
+// first_pass_done: the inner product has already formed u (HMult) and run the first
+// inverse pass on the rows ModDown transforms, so only their COLS pass is left.
 template <bool RESC>
-void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip)
+void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip, bool first_pass_done)
 {
     const Ws ws = ws_strides(c);
     const size_t es = c.ext_rows() * c.N, ps = (size_t)(c.L + 1) * c.N;
@@ -380,17 +382,21 @@ void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip)
     const dim3 eg(c.N / 256, 2 * B);
     if (RESC) {
         ProfScope _ps(c, "moddown_top", (uint64_t)6 * B);
-        launch_on(c, k_md_top_kernel, eg, 256, 0, ip, c.ws_acc, c.d_pc, hm.pinv, c.N, level, ps, es, ws);
-        check_launch("k_md_top");
+        if (!first_pass_done) {
+            launch_on(c, k_md_top_kernel, eg, 256, 0, ip, c.ws_acc, c.d_pc, hm.pinv, c.N, level, ps, es, ws);
+            check_launch("k_md_top");
+        }
         // rows l .. l + K of both accumulators of every item (the top limb u_k, then
         // the P rows) to the coefficient domain in one transform: row l times N^-1,
         // P row m times N^-1 (P / p_m)^-1
         LimbMap mp{c.ws_acc + (size_t)level * c.N, es, c.K + 1, 2 * B, 1, level, c.L + 1};
-        ntt_inv_mul(c, mp, c.d_md_outmul_top + (size_t)level * (c.K + 1));
+        if (first_pass_done) ntt_inv_cols_mul(c, mp, c.d_md_outmul_top + (size_t)level * (c.K + 1));
+        else ntt_inv_mul(c, mp, c.d_md_outmul_top + (size_t)level * (c.K + 1));
     } else {
         // P rows of both accumulators of every item to the coefficient domain, times (P / p_m)^-1
         LimbMap mp{c.ws_acc + (size_t)(level + 1) * c.N, es, c.K, 2 * B, 0, 0, c.L + 1};
-        ntt_inv_mul(c, mp, c.d_md_outmul);
+        if (first_pass_done) ntt_inv_cols_mul(c, mp, c.d_md_outmul);
+        else ntt_inv_mul(c, mp, c.d_md_outmul);
     }
     const uint64_t *hMP = c.d_ks + c.moddown_off + 2 * c.K;
     if (RESC) {
@@ -447,7 +453,7 @@ void ks_moddown(Ctx &c, int level, int B, const ItemPtrs &ip)
 }
 
 
-template void ks_moddown<true>(Ctx &, int, int, const ItemPtrs &);
-template void ks_moddown<false>(Ctx &, int, int, const ItemPtrs &);
+template void ks_moddown<true>(Ctx &, int, int, const ItemPtrs &, bool);
+template void ks_moddown<false>(Ctx &, int, int, const ItemPtrs &, bool);
 
 }  // namespace ppst
