@@ -44,12 +44,13 @@ HMULT_BYTES = (2 * 2 * 24 + 6 * 2 * 28 + 2 * 24) * 65536 * 8
 # writes, intermediates included) from ncu captures of the current kernels; the
 # per-launch traffic reported is this ratio times the launch's fused bytes.
 # Filled in from the capture of the kernel as it now stands (empty: none yet).
-# k_inner8 (8 words per thread, lazy accumulation, tile 4) in a single-item top-level
-# HMult (python -m paper_2508_12093_gb300.profcase hmult): 293.75 MB read + 19.41 MB
-# written against 293.6 MB of fused bytes (560 limbs of 512 KiB)
-DRAM_PER_FUSED = {"inner_chunks": (293.752 + 19.410) / 293.601}
+# k_inner8 (8 words per thread, lazy accumulation, tile 4, ModDown's first inverse
+# pass on the top and P rows) in a single-item top-level HMult (python -m
+# paper_2508_12093_gb300.profcase hmult): 300.05 MB read + 19.90 MB written against
+# 293.6 MB of fused bytes (560 limbs of 512 KiB; the top limb's d rows, 2 more, uncounted)
+DRAM_PER_FUSED = {"inner_chunks": (300.049 + 19.898) / 293.601}
 DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_inner8 in a single-item top-level HMult "
-               "(313.16 MB against 293.60 MB of fused bytes: 1.067), times the step's fused bytes per launch")
+               "(319.95 MB against 293.60 MB of fused bytes: 1.090), times the step's fused bytes per launch")
 
 
 def peaks():
